@@ -1,0 +1,360 @@
+"""Benchmark: joined-chain spin-flip attempts/s of the multicanonical weight
+iteration (Sec. 2 algorithm + Sec. 3.1 update) on one GB300.
+
+One step = one weight iteration of the whole hot path on the headline
+workload (L = 32, 16384 chains, 1e5 sweeps per chain, random start, seed 2):
+generation of every chain (Sec. 2 step 2), the joint by detailed balance
+(steps 3-5, speculation + resolution + segmented scan), the weight update
+(Eq. new_weight).  value = samples kept in the joined chain per second of
+device time (CUDA events on the job's stream).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (under torch.distributed.run): every rank runs an independent job
+(seed + rank) -- replicas, nothing exchanged on the data path; value = all
+ranks' kept samples over the slowest rank's time.  --impl reference times the
+CPU oracle, on bounded samples of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_0812_2964_gb300.workloads import WORKLOADS  # noqa: E402
+
+METRIC = "joined-chain spin-flip attempts/s"
+UNIT = "attempts/s"
+WORKLOAD = "L32_p16384"
+# Integer operations one single-spin-flip attempt needs (derivation in
+# the design doc): Philox4x32-10 amortised over its 4 words (10), aligned-
+# neighbour count (7), threshold index + load (2), compare (1), flip + level
+# update (2), dwell-time histogram (3).
+ALG_OPS_PER_ATTEMPT = 25
+SMS, SUBPARTITIONS, LANES = 152, 4, 32
+L2_FLUSH_BYTES = 256 << 20
+ORACLE_SAMPLE = dict(chains=128, sweeps=400)    # bounded CPU sample of the workload
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _traffic_record():
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=lambda: self.lines.extend(
+            ln.strip() for ln in self.proc.stdout), daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(self.REASONS, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def aggregate(kept_per_rank, seconds_per_rank):
+    """Whole-job throughput: kept samples of all ranks over the slowest rank."""
+    t = max(seconds_per_rank)
+    return (float(sum(kept_per_rank)) / t if t > 0 else 0.0), t
+
+
+def gather_max_sum(dist, world, kept, seconds, device):
+    """All ranks' (kept, seconds) -> (sum kept, max seconds), on the host side
+    of the run; used only for timing, never on the data path."""
+    if world == 1:
+        return kept, seconds
+    import torch
+    t = torch.tensor([float(kept), float(seconds)], dtype=torch.float64, device=device)
+    out = [torch.zeros_like(t) for _ in range(world)]
+    dist.all_gather(out, t)
+    ks = [float(o[0]) for o in out]
+    ss = [float(o[1]) for o in out]
+    return sum(ks), max(ss)
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(seconds_budget: float, L: int, seed: int, start: int):
+    """Kept samples per second of the plain oracle (generation + serial joint
+    + weight update) on a bounded sample of the workload, all host cores."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    p, S = ORACLE_SAMPLE["chains"], ORACLE_SAMPLE["sweeps"]
+    job = oracle.Job(L, p, seed, start)
+    kept, iters = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        kept += job.iteration(S, 0, cores)
+        iters += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_budget:
+            break
+    return {"value": kept / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"L={L}, {p} chains x {S} sweeps per iteration, {iters} weight iterations "
+                      f"from the workload's seed ({el:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = WORKLOADS[WORKLOAD]
+    import oracle
+
+    cores = os.cpu_count() or 1
+    p, S = ORACLE_SAMPLE["chains"], ORACLE_SAMPLE["sweeps"]
+    job = oracle.Job(w.L, p, w.seed, w.start)
+    for _ in range(args.warmup):
+        job.iteration(S, 0, cores)
+    kept = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        kept += job.iteration(S, 0, cores)
+    el = time.perf_counter() - t0
+    value = kept / el
+    sample = (f"L={w.L}, {p} chains x {S} sweeps per step (the workload has {w.chains} chains x "
+              f"{w.sweeps} sweeps), weight iterations {args.warmup + 1}..{args.warmup + args.steps}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "L": w.L, "chains": p,
+                                            "sweeps_per_iteration": S, "seed": w.seed},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_0812_2964_gb300 as mc
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    mc.build()
+    w = WORKLOADS[WORKLOAD]
+    S = args.sweeps or w.sweeps
+    p, N = w.chains, w.N
+    M = S * N
+    stream = torch.cuda.Stream(device=device)
+    job = mc.Job(w.L, p, w.seed + rank, w.start)
+    job.set_stream(stream.cuda_stream)
+    job.set_trace(True)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            job.run_sweeps(S)
+            job.join(want_length=False)
+            job.update_weights()
+            flush.fill_(1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    kept0 = job.info()["total_joined"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    launches0 = mc.mc_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    gen = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for i in range(args.steps):
+            gen[i][0].record(stream)
+            job.run_sweeps(S)              # generation kernel (+ 2 MB round-start copy)
+            gen[i][1].record(stream)
+            job.join(want_length=False)    # joint: search, resolution, correction, scan
+            job.update_weights()           # Eq. (new_weight) + threshold table
+            flush.fill_(1)                 # L2 flushed between timed steps
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = mc.mc_kernel_launches() - launches0
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    kept = job.info()["total_joined"] - kept0
+    gen_ms = [a.elapsed_time(b) for a, b in gen]
+    info = job.info()
+    if world > 1:
+        dist.barrier()
+    kept_all, t_max = gather_max_sum(dist, world, kept, elapsed, device)
+    value = kept_all / t_max
+
+    # ---- end to end through the public API, host buffers (pinned), per step:
+    # spins + weights in, run + join + histogram + update, weights + spins out
+    e2e_steps = max(1, args.e2e_steps)
+    nwords = p * w.L * ((w.L + 31) // 32)
+    spins_h = torch.empty(nwords, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    W_h = torch.empty(N + 1, dtype=torch.float64, pin_memory=True).numpy()
+    hist_h = torch.empty(N + 1, dtype=torch.int64, pin_memory=True).numpy()
+    mc.mc_get_spins(job.h, spins_h)
+    mc.mc_get_weights(job.h, W_h)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e2e_kept = 0
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        mc.mc_set_spins(job.h, spins_h)
+        mc.mc_set_weights(job.h, W_h)
+        mc.mc_run_sweeps(job.h, S)
+        e2e_kept += mc.mc_join(job.h, True)
+        mc.mc_histogram(job.h, hist_h)
+        mc.mc_update_weights(job.h)
+        mc.mc_get_weights(job.h, W_h)
+        mc.mc_get_spins(job.h, spins_h)
+    e2e_el = time.perf_counter() - t0
+    e2e_all, e2e_t = gather_max_sum(dist, world, e2e_kept, e2e_el, device)
+    h2d = nwords * 4 + (N + 1) * 8
+    d2h = 8 + (N + 1) * 8 + (N + 1) * 8 + nwords * 4
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (generation)
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    peak_ops = SMS * SUBPARTITIONS * LANES * sm_max * 1e6
+    gen_s = statistics.mean(gen_ms) / 1e3
+    gen_attempts = p * M
+    achieved = gen_attempts * ALG_OPS_PER_ATTEMPT / gen_s
+    tr = _traffic_record()
+    traffic = tr.get("bytes_per_launch") if tr.get("workload") == WORKLOAD and \
+        tr.get("sweeps") == S and tr.get("kernel_rev") == mc.KERNEL_REV else None
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(args.cpu_seconds, w.L, w.seed, w.start)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": w.L, "chains": p, "sweeps_per_iteration": S,
+                   "start": "random" if w.start else "all up", "seed": w.seed,
+                   "weight_iterations_timed": f"{args.warmup + 1}..{args.warmup + args.steps}",
+                   "l2": "flushed between steps (256 MB write)", "trace": "int32 per sweep",
+                   "launch": {"placement": ["registers", "shared"][info["placement"]],
+                              "chains_per_warp": info["chains_per_warp"],
+                              "warps_per_block": info["warps_per_block"]},
+                   "parallelism": f"replicas x{world}"},
+        "kept_fraction": kept / (args.steps * p * M),
+        "raw_attempts_per_s": args.steps * p * M * world / t_max,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
+                     "unit": "Gop/s", "frac": achieved / peak_ops, "traffic": traffic,
+                     "kernel": "gen_kernel (lattice rows in registers)",
+                     "kernel_ms": statistics.mean(gen_ms),
+                     "ops_per_attempt": ALG_OPS_PER_ATTEMPT,
+                     "peak_source": f"{SMS} SMs x {SUBPARTITIONS} sub-partitions x {LANES} lanes x "
+                                    f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"},
+        "e2e": {"value": e2e_all / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "last_joint": {k: info[k] for k in ("last_joined", "last_rejected", "last_mismatch",
+                                            "last_passes", "last_searched")},
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--sweeps", type=int, default=0, help="override sweeps per iteration")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

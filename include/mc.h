@@ -1,0 +1,169 @@
+/*
+ * mc.h -- C ABI of the GB300 library for parallel multicanonical Ising
+ * chains joined by detailed balance (T. Sugihara, J. Higo, H. Nakamura,
+ * "Parallelization of Markov Chain Generation and its Application to the
+ * Multicanonical Method").
+ *
+ * One job = p independent single-spin-flip Metropolis chains on the periodic
+ * L x L Ising model (Sec. 4.1, J = 1) under a common multicanonical weight
+ * w(E) = exp(W(E)) (Sec. 3.1; the library stores W = ln w, Sec. 4.2).  The
+ * weight-estimation loop of Sec. 2 / Sec. 3.1 is
+ *
+ *     mc_init -> repeat { mc_run_sweeps -> mc_join  [until h holds M_total]
+ *                         -> mc_histogram (optional) -> mc_update_weights }
+ *
+ * Conventions shared by every call:
+ *   - Energies E = -sum_<ij> s_i s_j = -2N + 4m, N = L*L; arrays indexed by
+ *     energy have N + 1 entries, entry m for E = -2N + 4m.
+ *   - One sample = the configuration after one single-spin-flip attempt;
+ *     sites are visited in typewriter order, so a round of S sweeps is
+ *     M = S*N samples per chain.
+ *   - Random numbers are Philox4x32-10 with key = seed; every draw has a
+ *     fixed counter, so results do not depend on launch shape, GPU or run.
+ *   - Spins are bit-packed: row y of chain c is ceil(L/32) uint32 words at
+ *     [(c*L + y)*ceil(L/32)]; bit x%32 of word x/32 is site (x, y), 1 = +1.
+ *   - All pointers in this header are HOST pointers owned by the caller and
+ *     only read or written during the call, unless stated otherwise.  The
+ *     job owns all its device memory.  Work is queued on the job's CUDA
+ *     stream; calls that return data synchronise that stream.
+ *   - A job handle is not thread-safe: use one handle per host thread.
+ *   - Every call returns MC_OK or a negative status; mc_last_error() gives a
+ *     message for the calling thread.  Nothing throws across the ABI.
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MC_OK 0
+#define MC_EINVAL (-1)   /* bad argument (size, range, null pointer) */
+#define MC_ENOMEM (-2)   /* device or host allocation failed */
+#define MC_ECUDA (-3)    /* a CUDA call failed (message has the CUDA error) */
+#define MC_ESTATE (-4)   /* call out of order (e.g. mc_join without a round) */
+#define MC_ETIMEOUT (-5) /* a bounded device wait gave up */
+
+typedef struct mc_job mc_job;
+
+typedef struct mc_info {
+  int L, N, n_chains, words_per_row;
+  uint64_t seed;
+  uint64_t attempts_per_chain; /* attempts each chain has made since mc_init */
+  uint32_t rounds_joined;      /* joints done so far */
+  int64_t last_sweeps;         /* sweeps of the most recent round */
+  int round_pending;           /* 1 between mc_run_sweeps and mc_join */
+  int carry_valid;             /* 0 until the first joint */
+  int carry_energy;            /* energy passed on to the next round's chain 0 */
+  int64_t last_joined;         /* samples kept by the most recent joint */
+  int64_t last_rejected;       /* chains of the most recent joint with none kept */
+  int64_t last_mismatch;       /* chains whose speculated joint input was wrong */
+  int64_t last_passes;         /* resolution passes of the most recent joint */
+  int64_t last_searched;       /* samples replayed while resolving */
+  int64_t total_joined;        /* samples kept by all joints of the job */
+  int placement;               /* 0: lattice in registers, 1: in shared memory */
+  int chains_per_warp, warps_per_block;
+  size_t device_bytes;         /* device memory held by the job */
+} mc_info;
+
+/* Create a job: Sec. 2 step 1 (h = 0, initial configurations C_1) and
+ * Sec. 3.1 (w^(1) = 1, i.e. W = 0).  4 <= L <= 128 with L % 4 == 0;
+ * 1 <= n_chains <= 2^24; start 0 = all spins up, 1 = random (Philox
+ * counter (q>>2, 0, chain, 2), word q&3 holds linear sites 32q..32q+31).
+ * Allocates all device memory of the job on the current device.  On error
+ * *out is NULL. */
+int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job **out);
+
+/* Release the job and its device memory (NULL is accepted). */
+void mc_free(mc_job *job);
+
+/* Queue the job's work on this CUDA stream (cudaStream_t passed as void*;
+ * NULL restores the job's own stream).  The caller keeps ownership. */
+int mc_set_stream(mc_job *job, void *cuda_stream);
+
+/* Enable (1) or disable (0) the per-sweep energy trace (int32 per chain per
+ * sweep, kept in device memory; read with mc_get_trace).  Default off. */
+int mc_set_trace(mc_job *job, int enabled);
+
+/* Sec. 2 step 2: every chain makes n_sweeps * N single-spin-flip Metropolis
+ * attempts under the current weight, continuing from its own last
+ * configuration (chains are never replaced).  Asynchronous on the job's
+ * stream.  MC_ESTATE if the previous round has not been joined.
+ * n_sweeps >= 1 and n_sweeps * N < 2^34. */
+int mc_run_sweeps(mc_job *job, int64_t n_sweeps);
+
+/* Sec. 2 steps 3-5 for the last round: chain i (in order) keeps its samples
+ * from the first one that passes the Metropolis test against the energy
+ * passed on by the chains before it (chain 0: by the previous round; in the
+ * job's first round chain 0 is kept whole); a chain with no such sample
+ * keeps nothing and passes on what it received.  Kept samples are added to
+ * h.  If joined_len is not NULL the call synchronises and stores the number
+ * of samples kept in this round.  MC_ESTATE without a pending round. */
+int mc_join(mc_job *job, int64_t *joined_len);
+
+/* The control of Sec. 5 / Fig. 2: concatenate the last round's chains whole,
+ * without the detailed-balance test at the joints.  Same contract as
+ * mc_join. */
+int mc_join_naive(mc_job *job, int64_t *joined_len);
+
+/* Copy the total histogram h(E) of the joined chain for the current weight
+ * (int64, n_bins must be N + 1) into out.  Synchronises. */
+int mc_histogram(mc_job *job, int64_t *out, int n_bins);
+
+/* Sec. 3.1 Eq. (new_weight) in logarithms (Sec. 4.2): W(E) -= ln h(E) where
+ * h(E) > 0, unchanged elsewhere; then h = 0 and the acceptance-threshold
+ * table is rebuilt.  MC_ESTATE while a round is pending.  Asynchronous. */
+int mc_update_weights(mc_job *job);
+
+/* W = ln w (double, n = N + 1).  mc_set_weights rebuilds the thresholds;
+ * MC_ESTATE while a round is pending.  mc_get_weights synchronises. */
+int mc_get_weights(mc_job *job, double *out, int n);
+int mc_set_weights(mc_job *job, const double *w, int n);
+
+/* Acceptance thresholds, planar: out[a*(N+1) + m] for the move from level m
+ * to m + a - 2 (a = number of aligned neighbours), n = 5*(N+1).  A uniform
+ * u is accepted iff u <= threshold.  Synchronises. */
+int mc_get_table(mc_job *job, uint32_t *out, int n);
+
+/* Bit-packed spins of all chains, n_words = n_chains * L * ceil(L/32).
+ * mc_set_spins masks unused high bits, recomputes the energies and is
+ * refused (MC_ESTATE) while a round is pending.  Both synchronise. */
+int mc_get_spins(mc_job *job, uint32_t *out, size_t n_words);
+int mc_set_spins(mc_job *job, const uint32_t *in, size_t n_words);
+
+/* Current energy of every chain (n = n_chains).  Synchronises. */
+int mc_get_energies(mc_job *job, int32_t *out, int n);
+
+/* Energy after each sweep of the last round, out[s*n_chains + c];
+ * n >= last_sweeps * n_chains; MC_ESTATE if the trace was off.  Syncs. */
+int mc_get_trace(mc_job *job, int32_t *out, size_t n);
+
+/* Result of the last joint: k[i] = first kept sample of chain i (1..M) or 0
+ * if none was kept; offsets[i] = position of chain i's kept segment in the
+ * joined chain of that round.  Either pointer may be NULL.  Synchronises. */
+int mc_get_join(mc_job *job, int64_t *k, int64_t *offsets, int n);
+
+/* Job state and statistics of the last joint.  Synchronises. */
+int mc_get_info(mc_job *job, mc_info *info);
+
+/* Choose how chains map to the GPU (placement 0 = registers, L <= 32;
+ * 1 = shared memory), chains per warp 1..32, warps per block 1..4.  The
+ * dynamics and all results are independent of this choice. */
+int mc_set_launch_shape(mc_job *job, int placement, int chains_per_warp, int warps_per_block);
+
+/* Wait for the job's queued work. */
+int mc_sync(mc_job *job);
+
+/* Number of kernels this library has launched since it was loaded. */
+uint64_t mc_kernel_launches(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *mc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MC_H */

@@ -1,0 +1,325 @@
+"""Python binding of libmcgpu (include/mc.h): parallel multicanonical Ising
+chains joined by detailed balance, on one GB300 (sm_103a).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  If the library has not been built (``build()``) or cannot be
+loaded, every call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+from .build import build
+
+__all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + [
+    "mc_init", "mc_free", "mc_set_stream", "mc_set_trace", "mc_run_sweeps", "mc_join",
+    "mc_join_naive", "mc_histogram", "mc_update_weights", "mc_get_weights", "mc_set_weights",
+    "mc_get_table", "mc_get_spins", "mc_set_spins", "mc_get_energies", "mc_get_trace",
+    "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error"]
+
+# revision of the generation kernel; bump when it changes (profiles record it)
+KERNEL_REV = "gen-1"
+
+MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ESTATE, MC_ETIMEOUT = 0, -1, -2, -3, -4, -5
+_NAMES = {MC_EINVAL: "MC_EINVAL", MC_ENOMEM: "MC_ENOMEM", MC_ECUDA: "MC_ECUDA",
+          MC_ESTATE: "MC_ESTATE", MC_ETIMEOUT: "MC_ETIMEOUT"}
+
+
+class McError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class mc_info(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("N", ctypes.c_int), ("n_chains", ctypes.c_int),
+                ("words_per_row", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("attempts_per_chain", ctypes.c_uint64), ("rounds_joined", ctypes.c_uint32),
+                ("last_sweeps", ctypes.c_int64), ("round_pending", ctypes.c_int),
+                ("carry_valid", ctypes.c_int), ("carry_energy", ctypes.c_int),
+                ("last_joined", ctypes.c_int64), ("last_rejected", ctypes.c_int64),
+                ("last_mismatch", ctypes.c_int64), ("last_passes", ctypes.c_int64),
+                ("last_searched", ctypes.c_int64), ("total_joined", ctypes.c_int64),
+                ("placement", ctypes.c_int),
+                ("chains_per_warp", ctypes.c_int), ("warps_per_block", ctypes.c_int),
+                ("device_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib():
+    """Load libmcgpu.so (built in-tree by ``build()``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing: run paper_0812_2964_gb300.build() first")
+        L = ctypes.CDLL(_LIB_PATH)
+        sig = {
+            "mc_init": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                       ctypes.POINTER(_vp)]),
+            "mc_free": (None, [_vp]),
+            "mc_set_stream": (ctypes.c_int, [_vp, _vp]),
+            "mc_set_trace": (ctypes.c_int, [_vp, ctypes.c_int]),
+            "mc_run_sweeps": (ctypes.c_int, [_vp, ctypes.c_int64]),
+            "mc_join": (ctypes.c_int, [_vp, _i64p]),
+            "mc_join_naive": (ctypes.c_int, [_vp, _i64p]),
+            "mc_histogram": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+            "mc_update_weights": (ctypes.c_int, [_vp]),
+            "mc_get_weights": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+            "mc_set_weights": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+            "mc_get_table": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+            "mc_get_spins": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+            "mc_set_spins": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+            "mc_get_energies": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+            "mc_get_trace": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+            "mc_get_join": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+            "mc_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(mc_info)]),
+            "mc_set_launch_shape": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+            "mc_sync": (ctypes.c_int, [_vp]),
+            "mc_kernel_launches": (ctypes.c_uint64, []),
+            "mc_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != MC_OK:
+        raise McError(rc, lib().mc_last_error().decode(errors="replace"))
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# ------------------------------------------------------------ C-ABI names
+def mc_init(L: int, n_chains: int, seed: int, start: int = 1):
+    h = _vp()
+    _check(lib().mc_init(L, n_chains, seed, start, ctypes.byref(h)))
+    return h
+
+
+def mc_free(job):
+    lib().mc_free(job)
+
+
+def mc_set_stream(job, stream_handle: int | None):
+    _check(lib().mc_set_stream(job, _vp(stream_handle or 0)))
+
+
+def mc_set_trace(job, enabled: bool):
+    _check(lib().mc_set_trace(job, 1 if enabled else 0))
+
+
+def mc_run_sweeps(job, n_sweeps: int):
+    _check(lib().mc_run_sweeps(job, n_sweeps))
+
+
+def mc_join(job, want_length: bool = True):
+    v = ctypes.c_int64(0)
+    _check(lib().mc_join(job, ctypes.byref(v) if want_length else None))
+    return int(v.value) if want_length else None
+
+
+def mc_join_naive(job, want_length: bool = True):
+    v = ctypes.c_int64(0)
+    _check(lib().mc_join_naive(job, ctypes.byref(v) if want_length else None))
+    return int(v.value) if want_length else None
+
+
+def mc_histogram(job, out: np.ndarray):
+    assert out.dtype == np.int64 and out.flags.c_contiguous
+    _check(lib().mc_histogram(job, _ptr(out), out.size))
+    return out
+
+
+def mc_update_weights(job):
+    _check(lib().mc_update_weights(job))
+
+
+def mc_get_weights(job, out: np.ndarray):
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    _check(lib().mc_get_weights(job, _ptr(out), out.size))
+    return out
+
+
+def mc_set_weights(job, w: np.ndarray):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    _check(lib().mc_set_weights(job, _ptr(w), w.size))
+
+
+def mc_get_table(job, out: np.ndarray):
+    assert out.dtype == np.uint32 and out.flags.c_contiguous
+    _check(lib().mc_get_table(job, _ptr(out), out.size))
+    return out
+
+
+def mc_get_spins(job, out: np.ndarray):
+    assert out.dtype == np.uint32 and out.flags.c_contiguous
+    _check(lib().mc_get_spins(job, _ptr(out), out.size))
+    return out
+
+
+def mc_set_spins(job, words: np.ndarray):
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    _check(lib().mc_set_spins(job, _ptr(w), w.size))
+
+
+def mc_get_energies(job, out: np.ndarray):
+    assert out.dtype == np.int32 and out.flags.c_contiguous
+    _check(lib().mc_get_energies(job, _ptr(out), out.size))
+    return out
+
+
+def mc_get_trace(job, out: np.ndarray):
+    assert out.dtype == np.int32 and out.flags.c_contiguous
+    _check(lib().mc_get_trace(job, _ptr(out), out.size))
+    return out
+
+
+def mc_get_join(job, k: np.ndarray | None, offsets: np.ndarray | None, n: int):
+    _check(lib().mc_get_join(job, _ptr(k) if k is not None else None,
+                             _ptr(offsets) if offsets is not None else None, n))
+
+
+def mc_get_info(job) -> mc_info:
+    info = mc_info()
+    _check(lib().mc_get_info(job, ctypes.byref(info)))
+    return info
+
+
+def mc_set_launch_shape(job, placement: int, chains_per_warp: int, warps_per_block: int):
+    _check(lib().mc_set_launch_shape(job, placement, chains_per_warp, warps_per_block))
+
+
+def mc_sync(job):
+    _check(lib().mc_sync(job))
+
+
+def mc_last_error() -> str:
+    return lib().mc_last_error().decode(errors="replace")
+
+
+def mc_kernel_launches() -> int:
+    return int(lib().mc_kernel_launches())
+
+
+# ------------------------------------------------------------ convenience
+class Job:
+    """One weight-estimation job (numpy in, numpy out)."""
+
+    def __init__(self, L: int, n_chains: int, seed: int, start: int = 1):
+        self.L, self.p, self.seed = L, n_chains, seed
+        self.N = L * L
+        self.wd = (L + 31) // 32
+        self.h = mc_init(L, n_chains, seed, start)
+
+    def close(self):
+        if getattr(self, "h", None):
+            mc_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_trace(self, on=True):
+        mc_set_trace(self.h, on)
+
+    def set_stream(self, handle):
+        mc_set_stream(self.h, handle)
+
+    def set_launch_shape(self, placement, cpw, wpb):
+        mc_set_launch_shape(self.h, placement, cpw, wpb)
+
+    def run_sweeps(self, S: int):
+        mc_run_sweeps(self.h, S)
+
+    def join(self, want_length=True):
+        return mc_join(self.h, want_length)
+
+    def join_naive(self, want_length=True):
+        return mc_join_naive(self.h, want_length)
+
+    def update_weights(self):
+        mc_update_weights(self.h)
+
+    def iteration(self, S: int, M_total: int = 0) -> int:
+        total = 0
+        while True:
+            self.run_sweeps(S)
+            total += self.join()
+            if total >= M_total:
+                break
+        self.update_weights()
+        return total
+
+    @property
+    def hist(self):
+        return mc_histogram(self.h, np.zeros(self.N + 1, np.int64))
+
+    @property
+    def weights(self):
+        return mc_get_weights(self.h, np.zeros(self.N + 1, np.float64))
+
+    @weights.setter
+    def weights(self, w):
+        mc_set_weights(self.h, w)
+
+    @property
+    def table(self):
+        """Thresholds as [m][a] (a = aligned neighbours)."""
+        t = mc_get_table(self.h, np.zeros(5 * (self.N + 1), np.uint32))
+        return t.reshape(5, self.N + 1).T.copy()
+
+    @property
+    def spin_words(self):
+        return mc_get_spins(self.h, np.zeros(self.p * self.L * self.wd, np.uint32)).reshape(
+            self.p, self.L, self.wd)
+
+    @spin_words.setter
+    def spin_words(self, w):
+        mc_set_spins(self.h, np.asarray(w, np.uint32).reshape(-1))
+
+    @property
+    def energies(self):
+        return mc_get_energies(self.h, np.zeros(self.p, np.int32))
+
+    @property
+    def trace(self):
+        S = self.info()["last_sweeps"]
+        return mc_get_trace(self.h, np.zeros(S * self.p, np.int32)).reshape(S, self.p)
+
+    @property
+    def k(self):
+        k = np.zeros(self.p, np.int64)
+        mc_get_join(self.h, k, None, self.p)
+        return k
+
+    @property
+    def offsets(self):
+        o = np.zeros(self.p, np.int64)
+        mc_get_join(self.h, None, o, self.p)
+        return o
+
+    def info(self):
+        return mc_get_info(self.h).as_dict()
+
+    def sync(self):
+        mc_sync(self.h)

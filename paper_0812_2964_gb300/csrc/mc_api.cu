@@ -1,0 +1,385 @@
+// C ABI (include/mc.h): job lifetime, device memory, stream ordering and
+// argument checking around the kernels of mc_kernels.cu.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mc.h"
+#include "mc_internal.h"
+
+using mcgpu::DevJob;
+using mcgpu::LaunchShape;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? MC_ENOMEM : MC_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e),
+              cudaGetErrorString(e));
+}
+
+#define MC_CUDA(call, what)                  \
+  do {                                       \
+    cudaError_t e_ = (call);                 \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+}  // namespace
+
+struct mc_job {
+  DevJob d;
+  int L, N, p, wd, start;
+  uint64_t seed;
+  cudaStream_t own_stream = nullptr, stream = nullptr;
+  int device = 0, num_sms = 0;
+  uint64_t t = 0;       // attempts per chain so far
+  uint32_t r = 0;       // joints done
+  int64_t last_S = 0;
+  bool pending = false;
+  bool trace_on = false;
+  bool trace_valid = false;
+  size_t trace_cap = 0;  // int32 elements
+  LaunchShape shape;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+template <class T>
+int dalloc(mc_job* j, T** p, size_t count) {
+  void* v = nullptr;
+  const size_t b = sizeof(T) * (count ? count : 1);
+  cudaError_t e = cudaMalloc(&v, b);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  j->allocs.push_back(v);
+  j->bytes += b;
+  *p = static_cast<T*>(v);
+  return MC_OK;
+}
+
+void free_all(mc_job* j) {
+  for (void* v : j->allocs) cudaFree(v);
+  j->allocs.clear();
+  if (j->d.trace) cudaFree(j->d.trace);
+  j->d.trace = nullptr;
+  if (j->own_stream) cudaStreamDestroy(j->own_stream);
+  j->own_stream = nullptr;
+}
+
+int check_job(mc_job* j) {
+  if (!j) return fail(MC_EINVAL, "null job");
+  return MC_OK;
+}
+
+int sync(mc_job* j, const char* what) {
+  MC_CUDA(cudaStreamSynchronize(j->stream), what);
+  return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mc_last_error(void) { return g_err.c_str(); }
+
+uint64_t mc_kernel_launches(void) { return mcgpu::launches_add(0); }
+
+int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
+  if (!out) return fail(MC_EINVAL, "out is null");
+  *out = nullptr;
+  if (L < 4 || L > 128 || (L % 4) != 0) return fail(MC_EINVAL, "L=%d: need 4 <= L <= 128, L %% 4 == 0", L);
+  if (n_chains < 1 || n_chains > (1 << 24)) return fail(MC_EINVAL, "n_chains=%d out of range", n_chains);
+  if (start != 0 && start != 1) return fail(MC_EINVAL, "start=%d: 0 (all up) or 1 (random)", start);
+  mc_job* j = new (std::nothrow) mc_job();
+  if (!j) return fail(MC_ENOMEM, "host allocation");
+  j->L = L;
+  j->N = L * L;
+  j->p = n_chains;
+  j->wd = (L + 31) / 32;
+  j->start = start;
+  j->seed = seed;
+  int rc = MC_OK;
+  cudaError_t e = cudaGetDevice(&j->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&j->num_sms, cudaDevAttrMultiProcessorCount, j->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&j->own_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "device setup");
+    free_all(j);
+    delete j;
+    return rc;
+  }
+  j->stream = j->own_stream;
+  DevJob& d = j->d;
+  std::memset(&d, 0, sizeof d);
+  d.L = L;
+  d.N = j->N;
+  d.np1 = j->N + 1;
+  d.wd = j->wd;
+  d.p = n_chains;
+  d.key0 = static_cast<uint32_t>(seed);
+  d.key1 = static_cast<uint32_t>(seed >> 32);
+  const size_t lat = static_cast<size_t>(n_chains) * L * j->wd;
+  const size_t np1 = static_cast<size_t>(d.np1);
+  if ((rc = dalloc(j, &d.spins, lat)) || (rc = dalloc(j, &d.spins0, lat)) || (rc = dalloc(j, &d.m, n_chains)) ||
+      (rc = dalloc(j, &d.m0, n_chains)) || (rc = dalloc(j, &d.W, np1)) || (rc = dalloc(j, &d.T, 5 * np1)) ||
+      (rc = dalloc(j, &d.h, np1)) || (rc = dalloc(j, &d.hgen, np1)) || (rc = dalloc(j, &d.dpre, np1)) ||
+      (rc = dalloc(j, &d.k, n_chains)) || (rc = dalloc(j, &d.kspec, n_chains)) ||
+      (rc = dalloc(j, &d.xused, n_chains)) || (rc = dalloc(j, &d.tj, static_cast<size_t>(n_chains) * np1)) ||
+      (rc = dalloc(j, &d.offsets, n_chains)) || (rc = dalloc(j, &d.work, n_chains)) ||
+      (rc = dalloc(j, &d.stats, mcgpu::kStatCount))) {
+    free_all(j);
+    delete j;
+    return rc;
+  }
+  cudaStream_t st = j->stream;
+  e = cudaMemsetAsync(d.W, 0, sizeof(double) * np1, st);  // w^(1) = 1
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.h, 0, sizeof(long long) * np1, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.hgen, 0, sizeof(unsigned long long) * np1, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.dpre, 0, sizeof(unsigned long long) * np1, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.stats, 0, sizeof(long long) * mcgpu::kStatCount, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.k, 0, sizeof(int64_t) * n_chains, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.offsets, 0, sizeof(int64_t) * n_chains, st);
+  if (e == cudaSuccess) e = mcgpu::k_init_lattice(d, start, st);
+  if (e == cudaSuccess) e = mcgpu::k_levels(d, st);
+  if (e == cudaSuccess) e = mcgpu::k_build_table(d, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "job initialisation");
+    free_all(j);
+    delete j;
+    return rc;
+  }
+  j->shape = mcgpu::default_shape(L, n_chains, j->num_sms);
+  *out = j;
+  return MC_OK;
+}
+
+void mc_free(mc_job* job) {
+  if (!job) return;
+  if (job->stream) cudaStreamSynchronize(job->stream);
+  free_all(job);
+  delete job;
+}
+
+int mc_set_stream(mc_job* job, void* cuda_stream) {
+  if (int rc = check_job(job)) return rc;
+  MC_CUDA(cudaStreamSynchronize(job->stream), "stream switch");
+  job->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : job->own_stream;
+  return MC_OK;
+}
+
+int mc_set_trace(mc_job* job, int enabled) {
+  if (int rc = check_job(job)) return rc;
+  if (job->pending) return fail(MC_ESTATE, "round pending");
+  job->trace_on = enabled != 0;
+  return MC_OK;
+}
+
+int mc_set_launch_shape(mc_job* job, int placement, int cpw, int wpb) {
+  if (int rc = check_job(job)) return rc;
+  LaunchShape s{placement, cpw, wpb};
+  if (!mcgpu::shape_supported(job->L, s))
+    return fail(MC_EINVAL, "launch shape (%d, %d, %d) not supported for L=%d", placement, cpw, wpb, job->L);
+  job->shape = s;
+  return MC_OK;
+}
+
+int mc_run_sweeps(mc_job* job, int64_t n_sweeps) {
+  if (int rc = check_job(job)) return rc;
+  if (job->pending) return fail(MC_ESTATE, "previous round not joined");
+  if (n_sweeps < 1) return fail(MC_EINVAL, "n_sweeps=%lld", static_cast<long long>(n_sweeps));
+  const int64_t M = n_sweeps * job->N;
+  if (n_sweeps > (int64_t(1) << 34) / job->N || M >= (int64_t(1) << 34))
+    return fail(MC_EINVAL, "n_sweeps * N must stay below 2^34");
+  DevJob& d = job->d;
+  if (job->trace_on) {
+    const size_t need = static_cast<size_t>(n_sweeps) * job->p;
+    if (need > job->trace_cap) {
+      if (d.trace) {
+        cudaStreamSynchronize(job->stream);
+        cudaFree(d.trace);
+        job->bytes -= job->trace_cap * sizeof(int32_t);
+        d.trace = nullptr;
+        job->trace_cap = 0;
+      }
+      void* v = nullptr;
+      MC_CUDA(cudaMalloc(&v, need * sizeof(int32_t)), "trace allocation");
+      d.trace = static_cast<int32_t*>(v);
+      job->trace_cap = need;
+      job->bytes += need * sizeof(int32_t);
+    }
+  }
+  const size_t lat = static_cast<size_t>(job->p) * job->L * job->wd;
+  MC_CUDA(cudaMemcpyAsync(d.spins0, d.spins, lat * sizeof(uint32_t), cudaMemcpyDeviceToDevice, job->stream),
+          "round-start copy");
+  MC_CUDA(cudaMemcpyAsync(d.m0, d.m, job->p * sizeof(int32_t), cudaMemcpyDeviceToDevice, job->stream),
+          "round-start copy");
+  MC_CUDA(mcgpu::k_generate(d, job->shape, job->t, n_sweeps, job->trace_on, job->stream), "generation");
+  job->t += static_cast<uint64_t>(M);
+  job->last_S = n_sweeps;
+  job->pending = true;
+  job->trace_valid = job->trace_on;
+  return MC_OK;
+}
+
+static int join_common(mc_job* job, int64_t* joined_len, bool naive) {
+  if (int rc = check_job(job)) return rc;
+  if (!job->pending) return fail(MC_ESTATE, "no round to join");
+  const int64_t M = job->last_S * job->N;
+  MC_CUDA(mcgpu::k_join(job->d, job->shape, job->t - static_cast<uint64_t>(M), job->last_S, job->r, naive,
+                        job->stream),
+          "joint");
+  job->r += 1;
+  job->pending = false;
+  if (joined_len) {
+    long long v = 0;
+    MC_CUDA(cudaMemcpyAsync(&v, job->d.stats + mcgpu::kStatJoined, sizeof v, cudaMemcpyDeviceToHost, job->stream),
+            "read joined length");
+    if (int rc = sync(job, "joint")) return rc;
+    *joined_len = v;
+  }
+  return MC_OK;
+}
+
+int mc_join(mc_job* job, int64_t* joined_len) { return join_common(job, joined_len, false); }
+int mc_join_naive(mc_job* job, int64_t* joined_len) { return join_common(job, joined_len, true); }
+
+int mc_histogram(mc_job* job, int64_t* out, int n_bins) {
+  if (int rc = check_job(job)) return rc;
+  if (!out || n_bins != job->N + 1) return fail(MC_EINVAL, "histogram needs N+1 = %d bins", job->N + 1);
+  MC_CUDA(cudaMemcpyAsync(out, job->d.h, sizeof(int64_t) * n_bins, cudaMemcpyDeviceToHost, job->stream),
+          "histogram copy");
+  return sync(job, "histogram");
+}
+
+int mc_update_weights(mc_job* job) {
+  if (int rc = check_job(job)) return rc;
+  if (job->pending) return fail(MC_ESTATE, "round pending: join first");
+  MC_CUDA(mcgpu::k_update_weights(job->d, job->stream), "weight update");
+  return MC_OK;
+}
+
+int mc_get_weights(mc_job* job, double* out, int n) {
+  if (int rc = check_job(job)) return rc;
+  if (!out || n != job->N + 1) return fail(MC_EINVAL, "weights need N+1 = %d entries", job->N + 1);
+  MC_CUDA(cudaMemcpyAsync(out, job->d.W, sizeof(double) * n, cudaMemcpyDeviceToHost, job->stream), "weights copy");
+  return sync(job, "weights");
+}
+
+int mc_set_weights(mc_job* job, const double* w, int n) {
+  if (int rc = check_job(job)) return rc;
+  if (job->pending) return fail(MC_ESTATE, "round pending");
+  if (!w || n != job->N + 1) return fail(MC_EINVAL, "weights need N+1 = %d entries", job->N + 1);
+  MC_CUDA(cudaMemcpyAsync(job->d.W, w, sizeof(double) * n, cudaMemcpyHostToDevice, job->stream), "weights copy");
+  MC_CUDA(mcgpu::k_build_table(job->d, job->stream), "table");
+  return sync(job, "set weights");
+}
+
+int mc_get_table(mc_job* job, uint32_t* out, int n) {
+  if (int rc = check_job(job)) return rc;
+  if (!out || n != 5 * (job->N + 1)) return fail(MC_EINVAL, "table needs 5*(N+1) entries");
+  MC_CUDA(cudaMemcpyAsync(out, job->d.T, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, job->stream), "table copy");
+  return sync(job, "table");
+}
+
+int mc_get_spins(mc_job* job, uint32_t* out, size_t n_words) {
+  if (int rc = check_job(job)) return rc;
+  const size_t need = static_cast<size_t>(job->p) * job->L * job->wd;
+  if (!out || n_words != need) return fail(MC_EINVAL, "spins need %zu words", need);
+  MC_CUDA(cudaMemcpyAsync(out, job->d.spins, need * 4, cudaMemcpyDeviceToHost, job->stream), "spins copy");
+  return sync(job, "spins");
+}
+
+int mc_set_spins(mc_job* job, const uint32_t* in, size_t n_words) {
+  if (int rc = check_job(job)) return rc;
+  if (job->pending) return fail(MC_ESTATE, "round pending");
+  const size_t need = static_cast<size_t>(job->p) * job->L * job->wd;
+  if (!in || n_words != need) return fail(MC_EINVAL, "spins need %zu words", need);
+  const int lw = job->L - 32 * (job->wd - 1);
+  const uint32_t last_mask = lw == 32 ? 0xFFFFFFFFu : ((1u << lw) - 1u);
+  std::vector<uint32_t> tmp(in, in + need);
+  for (size_t i = job->wd - 1; i < need; i += job->wd) tmp[i] &= last_mask;
+  MC_CUDA(cudaMemcpyAsync(job->d.spins, tmp.data(), need * 4, cudaMemcpyHostToDevice, job->stream), "spins copy");
+  MC_CUDA(mcgpu::k_levels(job->d, job->stream), "levels");
+  return sync(job, "set spins");
+}
+
+int mc_get_energies(mc_job* job, int32_t* out, int n) {
+  if (int rc = check_job(job)) return rc;
+  if (!out || n != job->p) return fail(MC_EINVAL, "energies need n_chains entries");
+  MC_CUDA(cudaMemcpyAsync(out, job->d.m, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, job->stream), "levels copy");
+  if (int rc = sync(job, "energies")) return rc;
+  for (int i = 0; i < n; ++i) out[i] = 4 * out[i] - 2 * job->N;
+  return MC_OK;
+}
+
+int mc_get_trace(mc_job* job, int32_t* out, size_t n) {
+  if (int rc = check_job(job)) return rc;
+  if (!job->trace_valid || !job->d.trace) return fail(MC_ESTATE, "no trace recorded for the last round");
+  const size_t need = static_cast<size_t>(job->last_S) * job->p;
+  if (!out || n < need) return fail(MC_EINVAL, "trace needs %zu entries", need);
+  MC_CUDA(cudaMemcpyAsync(out, job->d.trace, need * 4, cudaMemcpyDeviceToHost, job->stream), "trace copy");
+  return sync(job, "trace");
+}
+
+int mc_get_join(mc_job* job, int64_t* k, int64_t* offsets, int n) {
+  if (int rc = check_job(job)) return rc;
+  if (n != job->p) return fail(MC_EINVAL, "need n_chains entries");
+  if (k) MC_CUDA(cudaMemcpyAsync(k, job->d.k, 8ull * n, cudaMemcpyDeviceToHost, job->stream), "k copy");
+  if (offsets)
+    MC_CUDA(cudaMemcpyAsync(offsets, job->d.offsets, 8ull * n, cudaMemcpyDeviceToHost, job->stream), "offsets copy");
+  return sync(job, "join results");
+}
+
+int mc_get_info(mc_job* job, mc_info* info) {
+  if (int rc = check_job(job)) return rc;
+  if (!info) return fail(MC_EINVAL, "info is null");
+  long long st[mcgpu::kStatCount];
+  MC_CUDA(cudaMemcpyAsync(st, job->d.stats, sizeof st, cudaMemcpyDeviceToHost, job->stream), "stats copy");
+  if (int rc = sync(job, "info")) return rc;
+  std::memset(info, 0, sizeof *info);
+  info->L = job->L;
+  info->N = job->N;
+  info->n_chains = job->p;
+  info->words_per_row = job->wd;
+  info->seed = job->seed;
+  info->attempts_per_chain = job->t;
+  info->rounds_joined = job->r;
+  info->last_sweeps = job->last_S;
+  info->round_pending = job->pending ? 1 : 0;
+  info->carry_valid = static_cast<int>(st[mcgpu::kStatCarryValid]);
+  info->carry_energy = info->carry_valid ? static_cast<int>(4 * st[mcgpu::kStatCarry] - 2 * job->N) : 0;
+  info->last_joined = st[mcgpu::kStatJoined];
+  info->last_rejected = st[mcgpu::kStatRejected];
+  info->last_mismatch = st[mcgpu::kStatMismatch];
+  info->last_passes = st[mcgpu::kStatPasses];
+  info->last_searched = st[mcgpu::kStatSearched];
+  info->total_joined = st[mcgpu::kStatJoinedTotal];
+  info->placement = job->shape.placement;
+  info->chains_per_warp = job->shape.cpw;
+  info->warps_per_block = job->shape.wpb;
+  info->device_bytes = job->bytes;
+  return MC_OK;
+}
+
+int mc_sync(mc_job* job) {
+  if (int rc = check_job(job)) return rc;
+  return sync(job, "sync");
+}
+
+}  // extern "C"

@@ -1,0 +1,475 @@
+// Templated chain kernels (generation, speculative joint search, resolution,
+// prefix correction) and their launchers.  Included by the instantiation
+// units mc_inst_*.cu, each of which compiles the kernels for a few lattice
+// sizes so that the library builds in parallel.
+#pragma once
+#include <algorithm>
+
+#include "mc_chain.cuh"
+#include "mc_internal.h"
+
+namespace mcgpu {
+
+inline unsigned blocks_for(long long n, int t) { return static_cast<unsigned>((n + t - 1) / t); }
+
+// ------------------------------------------------------------------ runners
+// A chain's lattice during a sweep, in registers (L <= 32, one word per row;
+// rows rotate through the register array so that every index is static) or
+// in shared memory (any L; per-thread column with a stride of the number of
+// lanes that hold chains, so that a warp's accesses hit distinct banks).
+template <int L>
+struct RegRunner {
+  static constexpr int WD = 1;
+  uint32_t R[L];
+  __device__ __forceinline__ void load(const uint32_t* __restrict__ g) {
+#pragma unroll
+    for (int y = 0; y < L; ++y) R[y] = g[y];
+  }
+  __device__ __forceinline__ void store(uint32_t* __restrict__ g) const {
+#pragma unroll
+    for (int y = 0; y < L; ++y) g[y] = R[y];
+  }
+  template <bool EARLY, class Hook>
+  __device__ __forceinline__ void sweep(int& m, uint64_t& blk, const uint32_t* __restrict__ T, int np1,
+                                        uint32_t chain, uint32_t k0, uint32_t k1, Hook& hk) {
+#pragma unroll 1
+    for (int y = 0; y < L; ++y) {
+      uint32_t cur[1] = {R[0]};
+      const uint32_t up[1] = {R[L - 1]};
+      const uint32_t dn[1] = {R[1]};
+      sweep_row<1>(cur, up, dn, L, m, T, np1, blk, chain, k0, k1, hk);
+#pragma unroll
+      for (int i = 0; i < L - 1; ++i) R[i] = R[i + 1];
+      R[L - 1] = cur[0];
+      if constexpr (EARLY) {
+        if (hk.done) break;
+      }
+    }
+  }
+};
+
+template <int WD>
+struct SmemRunner {
+  uint32_t* lat;  // this chain's column
+  int stride, L;
+  __device__ __forceinline__ void load(const uint32_t* __restrict__ g) {
+    for (int i = 0; i < L * WD; ++i) lat[i * stride] = g[i];
+  }
+  __device__ __forceinline__ void store(uint32_t* __restrict__ g) const {
+    for (int i = 0; i < L * WD; ++i) g[i] = lat[i * stride];
+  }
+  template <bool EARLY, class Hook>
+  __device__ __forceinline__ void sweep(int& m, uint64_t& blk, const uint32_t* __restrict__ T, int np1,
+                                        uint32_t chain, uint32_t k0, uint32_t k1, Hook& hk) {
+#pragma unroll 1
+    for (int y = 0; y < L; ++y) {
+      const int ym = (y == 0) ? L - 1 : y - 1, yp = (y + 1 == L) ? 0 : y + 1;
+      uint32_t cur[WD], up[WD], dn[WD];
+#pragma unroll
+      for (int w = 0; w < WD; ++w) {
+        cur[w] = lat[(y * WD + w) * stride];
+        up[w] = lat[(ym * WD + w) * stride];
+        dn[w] = lat[(yp * WD + w) * stride];
+      }
+      sweep_row<WD>(cur, up, dn, L, m, T, np1, blk, chain, k0, k1, hk);
+#pragma unroll
+      for (int w = 0; w < WD; ++w) lat[(y * WD + w) * stride] = cur[w];
+      if constexpr (EARLY) {
+        if (hk.done) break;
+      }
+    }
+  }
+};
+
+// Shared-memory plan of a block: [table (opt.)][histogram u32][lattices].
+struct SmemPlan {
+  int table_words, hist_words, lat_words;
+};
+
+__host__ __device__ inline SmemPlan smem_plan(int L, int placement, int cpw, int wpb, bool tsmem, bool hist) {
+  const int np1 = L * L + 1, wd = (L + 31) / 32;
+  SmemPlan s;
+  s.table_words = tsmem ? ((5 * np1 + 3) & ~3) : 0;
+  s.hist_words = hist ? ((np1 + 3) & ~3) : 0;
+  s.lat_words = placement == kPlaceSmem ? cpw * wpb * L * wd : 0;
+  return s;
+}
+
+struct BlockCtx {
+  const uint32_t* T;
+  uint32_t* hist;
+  uint32_t* lat;
+  int chain, lane, warp, slot, nslot;
+  bool active;
+};
+
+template <bool TSMEM>
+__device__ __forceinline__ BlockCtx block_setup(const DevJob& j, const SmemPlan& sp, int cpw, int first_chain,
+                                                bool zero_hist) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  BlockCtx b;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if (TSMEM)
+    for (int i = tid; i < 5 * j.np1; i += nthr) smem[i] = j.T[i];
+  b.T = TSMEM ? smem : j.T;
+  b.hist = smem + sp.table_words;
+  if (zero_hist)
+    for (int i = tid; i < sp.hist_words; i += nthr) b.hist[i] = 0u;
+  b.lat = smem + sp.table_words + sp.hist_words;
+  b.lane = tid & 31;
+  b.warp = tid >> 5;
+  b.slot = b.warp * cpw + b.lane;
+  b.nslot = (nthr >> 5) * cpw;
+  b.chain = first_chain + b.slot;
+  b.active = b.lane < cpw && b.chain < j.p;
+  return b;
+}
+
+// ------------------------------------------------------------------ generation
+struct NoSweepHook {
+  __device__ __forceinline__ void operator()(int64_t, int) const {}
+};
+
+template <int L>
+struct RunnerFactoryReg {
+  __device__ __forceinline__ static RegRunner<L> make(const BlockCtx&, int) { return RegRunner<L>(); }
+};
+template <int WD>
+struct RunnerFactorySmem {
+  __device__ __forceinline__ static SmemRunner<WD> make(const BlockCtx& b, int L) {
+    SmemRunner<WD> r;
+    r.lat = b.lat + b.slot;
+    r.stride = b.nslot;
+    r.L = L;
+    return r;
+  }
+};
+
+// Step 2: every chain performs S sweeps (M = S N attempts) under the current
+// weight; per-level dwell counts accumulate in shared memory, then in the
+// round histogram hgen.  trace[s][c] = energy after sweep s.
+template <class Factory, bool TSMEM>
+__global__ void __launch_bounds__(128) gen_kernel(const DevJob j, const int cpw, const uint64_t t0,
+                                                  const int64_t S, const int64_t flushF, const int do_trace) {
+  const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, true);
+  const int first = blockIdx.x * (blockDim.x >> 5) * cpw;
+  BlockCtx b = block_setup<TSMEM>(j, sp, cpw, first, true);
+  auto run = Factory::make(b, j.L);
+  __syncthreads();
+  int m = 0;
+  uint64_t blk = t0 >> 2;
+  GenHook hk{b.hist, 0u};
+  if (b.active) {
+    run.load(j.spins + static_cast<size_t>(b.chain) * j.L * j.wd);
+    m = j.m[b.chain];
+  }
+  for (int64_t s = 0; s < S; ++s) {
+    if (b.active) {
+      run.template sweep<false>(m, blk, b.T, j.np1, static_cast<uint32_t>(b.chain), j.key0, j.key1, hk);
+      if (do_trace) j.trace[s * j.p + b.chain] = 4 * m - 2 * j.N;
+    }
+    if (flushF > 0 && (s + 1) % flushF == 0 && s + 1 < S) {
+      if (b.active) hk.flush(m);
+      __syncthreads();
+      for (int i = threadIdx.x; i < j.np1; i += blockDim.x) {
+        const uint32_t v = b.hist[i];
+        if (v) {
+          atomicAdd(&j.hgen[i], static_cast<unsigned long long>(v));
+          b.hist[i] = 0u;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (b.active) {
+    hk.flush(m);
+    run.store(j.spins + static_cast<size_t>(b.chain) * j.L * j.wd);
+    j.m[b.chain] = m;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < j.np1; i += blockDim.x) {
+    const uint32_t v = b.hist[i];
+    if (v) atomicAdd(&j.hgen[i], static_cast<unsigned long long>(v));
+  }
+}
+
+// ------------------------------------------------------------------ joint: replays
+// Replay chain i from its round-start configuration with the round's flip
+// counters and run a hook over its samples.
+template <class Factory, class Hook>
+__device__ __forceinline__ void replay_chain(const DevJob& j, const BlockCtx& b, int i, uint64_t t0, int64_t S,
+                                             Hook& hk) {
+  auto run = Factory::make(b, j.L);
+  run.load(j.spins0 + static_cast<size_t>(i) * j.L * j.wd);
+  int m = j.m0[i];
+  uint64_t blk = t0 >> 2;
+  for (int64_t s = 0; s < S && !hk.done; ++s)
+    run.template sweep<true>(m, blk, b.T, j.np1, static_cast<uint32_t>(i), j.key0, j.key1, hk);
+}
+
+// Speculative joint search (step 4 with input = last level of chain i-1):
+// k of the first accepted sample, and the discarded prefix added to dpre.
+template <class Factory, bool TSMEM>
+__global__ void __launch_bounds__(128) spec_kernel(const DevJob j, const int cpw, const uint64_t t0,
+                                                   const int64_t S, const uint32_t r) {
+  const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, false);
+  const int first = blockIdx.x * (blockDim.x >> 5) * cpw;
+  BlockCtx b = block_setup<TSMEM>(j, sp, cpw, first, false);
+  __syncthreads();
+  if (!b.active) return;
+  const int i = b.chain;
+  const int x = j.xused[i];
+  int64_t k;
+  if (x < 0) {
+    k = 1;  // job's first joint: chain 0 is kept whole
+  } else {
+    SearchHook<true> hk;
+    hk.tj = j.tj + static_cast<size_t>(i) * j.np1;
+    hk.D = j.dpre;
+    hk.k = 0;
+    hk.M = S * j.N;
+    hk.found = 0;
+    hk.chain = static_cast<uint32_t>(i);
+    hk.r = r;
+    hk.k0 = j.key0;
+    hk.k1 = j.key1;
+    hk.jr = make_uint4(0u, 0u, 0u, 0u);
+    hk.cur_level = -1;
+    hk.run = 0u;
+    hk.done = false;
+    replay_chain<Factory>(j, b, i, t0, S, hk);
+    k = hk.found;
+  }
+  j.k[i] = k;
+  j.kspec[i] = k;
+}
+
+// Block-wide inclusive max-scan of int values (one value per element, p
+// elements, each thread a contiguous range), used for "last accepted chain
+// before i".
+static __device__ void block_last_accepted(const DevJob& j, int* s_tmp) {
+  // s_tmp: blockDim.x ints.  Writes into j.work[i] the index of the last
+  // chain < i whose k > 0 (or -1).
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int per = (j.p + nt - 1) / nt;
+  const int lo = min(j.p, t * per), hi = min(j.p, lo + per);
+  int last = -1;
+  for (int i = lo; i < hi; ++i)
+    if (j.k[i] > 0) last = i;
+  s_tmp[t] = last;
+  __syncthreads();
+  for (int off = 1; off < nt; off <<= 1) {
+    const int v = (t >= off) ? s_tmp[t - off] : -1;
+    __syncthreads();
+    s_tmp[t] = max(s_tmp[t], v);
+    __syncthreads();
+  }
+  int run = (t > 0) ? s_tmp[t - 1] : -1;  // exclusive prefix
+  for (int i = lo; i < hi; ++i) {
+    j.work[i] = run;
+    if (j.k[i] > 0) run = i;
+  }
+  __syncthreads();
+}
+
+// Resolution of the speculation, one block: the actual input of chain i is
+// the last level of the nearest chain before it that kept samples (or the
+// carry).  Chains whose k was computed for another input are searched again
+// (their new thresholds first), in parallel, until no input changes; each
+// pass settles at least the first such chain.  Also fixes the carry.
+template <class Factory, bool TSMEM>
+__global__ void __launch_bounds__(128) resolve_kernel(const DevJob j, const int cpw, const uint64_t t0,
+                                                      const int64_t S, const uint32_t r) {
+  const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, false);
+  BlockCtx b = block_setup<TSMEM>(j, sp, cpw, 0, false);
+  __shared__ int s_tmp[128];
+  __shared__ int s_count;
+  __syncthreads();
+  const int carry_in = j.stats[kStatCarryValid] ? static_cast<int>(j.stats[kStatCarry]) : -1;
+  long long searched = 0;
+  int passes = 0, mism_total = 0;
+  for (;;) {
+    block_last_accepted(j, s_tmp);
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    // list of chains whose input changed (j.work reused: first the scan
+    // result, then the list, written after the scan result was consumed)
+    for (int i = threadIdx.x; i < j.p; i += blockDim.x) {
+      const int last = j.work[i];
+      const int x = (last >= 0) ? j.m[last] : carry_in;
+      if (x != j.xused[i]) {
+        j.xused[i] = x;
+        j.k[i] = -1;  // marked: to be searched again
+        atomicAdd(&s_count, 1);
+      }
+    }
+    __syncthreads();
+    const int count = s_count;
+    if (count == 0 || passes > j.p) break;
+    ++passes;
+    mism_total += count;
+    // compact the marked chains into work[]
+    if (threadIdx.x == 0) {
+      int n = 0;
+      for (int i = 0; i < j.p; ++i)
+        if (j.k[i] == -1) j.work[n++] = i;
+    }
+    __syncthreads();
+    // thresholds of the new inputs
+    for (long long idx = threadIdx.x; idx < static_cast<long long>(count) * j.np1; idx += blockDim.x) {
+      const int i = j.work[idx / j.np1], mm = static_cast<int>(idx % j.np1);
+      const int x = j.xused[i];
+      j.tj[static_cast<size_t>(i) * j.np1 + mm] = (x < 0) ? 0xFFFFFFFFu : threshold_det(__dsub_rn(j.W[mm], j.W[x]));
+    }
+    __syncthreads();
+    if (b.active) {
+      for (int q = b.slot; q < count; q += b.nslot) {
+        const int i = j.work[q];
+        if (j.xused[i] < 0) {
+          j.k[i] = 1;
+          continue;
+        }
+        SearchHook<false> hk;
+        hk.tj = j.tj + static_cast<size_t>(i) * j.np1;
+        hk.D = nullptr;
+        hk.k = 0;
+        hk.M = S * j.N;
+        hk.found = 0;
+        hk.chain = static_cast<uint32_t>(i);
+        hk.r = r;
+        hk.k0 = j.key0;
+        hk.k1 = j.key1;
+        hk.jr = make_uint4(0u, 0u, 0u, 0u);
+        hk.cur_level = -1;
+        hk.run = 0u;
+        hk.done = false;
+        replay_chain<Factory>(j, b, i, t0, S, hk);
+        j.k[i] = hk.found;
+        searched += hk.k;
+      }
+    }
+    __syncthreads();
+  }
+  // carry for the next round: the last level of the last chain that kept samples
+  if (threadIdx.x == 0) {
+    int last = -1;
+    for (int i = j.p - 1; i >= 0; --i)
+      if (j.k[i] > 0) {
+        last = i;
+        break;
+      }
+    if (last >= 0) {
+      j.stats[kStatCarry] = j.m[last];
+      j.stats[kStatCarryValid] = 1;
+    }
+    j.stats[kStatMismatch] = mism_total;
+    j.stats[kStatPasses] = passes;
+  }
+  if (searched) atomicAdd(reinterpret_cast<unsigned long long*>(&j.stats[kStatSearched]),
+                          static_cast<unsigned long long>(searched));
+}
+
+// Chains whose final k differs from the speculated one: move the samples
+// between the two prefix ends into or out of the discarded histogram.
+template <class Factory, bool TSMEM>
+__global__ void __launch_bounds__(128) correct_kernel(const DevJob j, const int cpw, const uint64_t t0,
+                                                      const int64_t S) {
+  const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, false);
+  const int first = blockIdx.x * (blockDim.x >> 5) * cpw;
+  BlockCtx b = block_setup<TSMEM>(j, sp, cpw, first, false);
+  __syncthreads();
+  if (!b.active) return;
+  const int i = b.chain;
+  const int64_t M = S * j.N;
+  const int64_t ks = j.kspec[i], kf = j.k[i];
+  if (ks == kf) return;
+  const int64_t es = ks > 0 ? ks : M + 1, ef = kf > 0 ? kf : M + 1;
+  CorrectHook hk;
+  hk.D = j.dpre;
+  hk.k = 0;
+  hk.lo = min(es, ef);
+  hk.hi = max(es, ef);
+  hk.sign = (ef > es) ? 1ull : ~0ull;  // +1 or -1
+  hk.cur_level = -1;
+  hk.run = 0u;
+  hk.done = false;
+  replay_chain<Factory>(j, b, i, t0, S, hk);
+  hk.flush();
+}
+
+// ------------------------------------------------------------------ host-side launchers
+template <int L>
+struct RegF : RunnerFactoryReg<L> {
+  static constexpr int kPlacement = kPlaceReg;
+};
+template <int WD>
+struct SmemF : RunnerFactorySmem<WD> {
+  static constexpr int kPlacement = kPlaceSmem;
+};
+
+constexpr size_t kMaxSmem = 227 * 1024;
+
+inline bool table_fits(int L, const LaunchShape& s, bool hist) {
+  const SmemPlan sp = smem_plan(L, s.placement, s.cpw, s.wpb, true, hist);
+  return 4ull * (sp.table_words + sp.hist_words + sp.lat_words) <= kMaxSmem;
+}
+
+inline size_t plan_bytes(int L, const LaunchShape& s, bool tsmem, bool hist) {
+  const SmemPlan sp = smem_plan(L, s.placement, s.cpw, s.wpb, tsmem, hist);
+  return 4ull * (sp.table_words + sp.hist_words + sp.lat_words);
+}
+
+template <class F, bool TS>
+inline cudaError_t launch_gen_t(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S, bool trace,
+                                cudaStream_t st) {
+  const size_t bytes = plan_bytes(j.L, s, TS, true);
+  auto kern = gen_kernel<F, TS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e != cudaSuccess) return e;
+  const int per_block = s.cpw * s.wpb;
+  const unsigned grid = blocks_for(j.p, per_block);
+  // dwell counts are u32 in shared memory: flush before they can overflow
+  const long long per_sweep = static_cast<long long>(per_block) * j.N;
+  const int64_t flushF = std::max<int64_t>(1, 0xFFFFFFFFll / per_sweep);
+  kern<<<grid, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, S > flushF ? flushF : 0, trace ? 1 : 0);
+  launches_add(1);
+  return cudaGetLastError();
+}
+
+template <class F, bool TS>
+inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S, uint32_t r,
+                                 cudaStream_t st) {
+  const size_t bytes = plan_bytes(j.L, s, TS, false);
+  const int per_block = s.cpw * s.wpb;
+  const unsigned grid = blocks_for(j.p, per_block);
+  cudaError_t e = join_prelude(j, st);
+  if (e != cudaSuccess) return e;
+  auto ks = spec_kernel<F, TS>;
+  if ((e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=
+      cudaSuccess)
+    return e;
+  ks<<<grid, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r);
+  auto kr = resolve_kernel<F, TS>;
+  if ((e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=
+      cudaSuccess)
+    return e;
+  kr<<<1, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r);
+  auto kc = correct_kernel<F, TS>;
+  if ((e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=
+      cudaSuccess)
+    return e;
+  kc<<<grid, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S);
+  launches_add(3);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return join_finalize(j, S, st);
+}
+
+template <class F>
+inline cudaError_t dispatch_ts(const DevJob& j, const LaunchShape& s, bool gen, uint64_t t0, int64_t S, bool trace,
+                               uint32_t r, cudaStream_t st) {
+  const bool ts = table_fits(j.L, s, gen);
+  if (gen) return ts ? launch_gen_t<F, true>(j, s, t0, S, trace, st) : launch_gen_t<F, false>(j, s, t0, S, trace, st);
+  return ts ? launch_join_t<F, true>(j, s, t0, S, r, st) : launch_join_t<F, false>(j, s, t0, S, r, st);
+}
+
+}  // namespace mcgpu

@@ -1,0 +1,92 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace mcgpu {
+
+// Lattice placement of a chain during a sweep.
+enum Placement : int {
+  kPlaceReg = 0,   // one chain per thread, rows in registers (L <= 32)
+  kPlaceSmem = 1,  // one chain per thread, rows in shared memory (any L)
+};
+
+struct LaunchShape {
+  int placement;   // Placement
+  int cpw;         // chains per warp (1..32; lanes >= cpw idle)
+  int wpb;         // warps per block
+};
+
+// Device-resident state of one job (all pointers are device pointers).
+struct DevJob {
+  int L, N, np1, wd, p;
+  uint32_t key0, key1;
+  uint32_t* spins;     // [p][L][wd]
+  uint32_t* spins0;    // round-start copy
+  int32_t* m;          // [p] level now (after the round: level of sample M)
+  int32_t* m0;         // [p] level at round start
+  double* W;           // [np1]
+  uint32_t* T;         // [5][np1] flip thresholds
+  long long* h;        // [np1] histogram of the joined chain (this iteration)
+  unsigned long long* hgen;  // [np1] all samples of the round
+  unsigned long long* dpre;  // [np1] discarded prefixes of the round
+  int64_t* k;          // [p] first kept sample (0 = none) after the joint
+  int64_t* kspec;      // [p] first kept sample under the speculated input
+  int32_t* xused;      // [p] input level the current k was computed for (-1 = none)
+  uint32_t* tj;        // [p][np1] joint thresholds for each chain's input
+  int64_t* offsets;    // [p] position of each kept segment in the joined chain
+  int32_t* work;       // [p] scratch list of chains
+  int32_t* trace;      // [S][p] energy after each sweep (nullable)
+  long long* stats;    // [kStatCount] small device counters
+};
+
+enum StatIndex : int {
+  kStatCarry = 0,        // level passed on to the next round's chain 0
+  kStatCarryValid = 1,
+  kStatJoined = 2,       // samples kept in the last joint
+  kStatMismatch = 3,     // chains whose speculated input was wrong (last joint)
+  kStatPasses = 4,       // resolve passes of the last joint
+  kStatRejected = 5,     // chains with no kept sample (last joint)
+  kStatSearched = 6,     // samples replayed by the last joint's searches
+  kStatJoinedTotal = 7,  // samples kept by all joints of the job
+  kStatCount = 8
+};
+
+// ---- kernels (mc_kernels.cu) ----
+cudaError_t k_init_lattice(const DevJob& j, int start, cudaStream_t st);
+cudaError_t k_levels(const DevJob& j, cudaStream_t st);
+cudaError_t k_build_table(const DevJob& j, cudaStream_t st);
+cudaError_t k_update_weights(const DevJob& j, cudaStream_t st);
+cudaError_t k_generate(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S,
+                       bool trace, cudaStream_t st);
+cudaError_t k_join(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S, uint32_t r,
+                   bool naive, cudaStream_t st);
+
+// pieces of the joint shared by all lattice sizes
+cudaError_t join_prelude(const DevJob& j, cudaStream_t st);
+cudaError_t join_finalize(const DevJob& j, int64_t S, cudaStream_t st);
+
+// per-unit launchers of the templated chain kernels (mc_inst_*.cu)
+#define MC_CHAIN_UNIT(name)                                                                              \
+  cudaError_t name(const DevJob& j, const LaunchShape& s, bool gen, uint64_t t0, int64_t S, bool trace, \
+                   uint32_t r, cudaStream_t st)
+MC_CHAIN_UNIT(chain_kernels_reg_a);
+MC_CHAIN_UNIT(chain_kernels_reg_b);
+MC_CHAIN_UNIT(chain_kernels_reg_c);
+MC_CHAIN_UNIT(chain_kernels_smem_1);
+MC_CHAIN_UNIT(chain_kernels_smem_2);
+MC_CHAIN_UNIT(chain_kernels_smem_3);
+MC_CHAIN_UNIT(chain_kernels_smem_4);
+#undef MC_CHAIN_UNIT
+
+// launch shape chosen by default for (L, p)
+LaunchShape default_shape(int L, int p, int num_sms);
+bool shape_supported(int L, const LaunchShape& s);
+size_t gen_smem_bytes(int L, const LaunchShape& s, bool* table_in_smem);
+
+// total kernel launches issued by this library (for accounting)
+uint64_t launches_add(uint64_t n);
+
+}  // namespace mcgpu

@@ -1,0 +1,277 @@
+// Kernels of the hot path: initial lattices, threshold table, generation of
+// p independent chains (Sec. 2 step 2), the joint by detailed balance (steps
+// 3-5) as speculation + resolution + segmented scan, and the weight update
+// (Sec. 3.1 Eq. new_weight in logarithms, Sec. 4.2).
+#include <atomic>
+#include <algorithm>
+
+#include "mc_chain_kernels.cuh"
+
+namespace mcgpu {
+
+static std::atomic<uint64_t> g_launches{0};
+uint64_t launches_add(uint64_t n) { return g_launches.fetch_add(n) + n; }
+
+
+// ------------------------------------------------------------------ init
+// Step 1: C_1 all up, or random: bit (site & 31) of Philox word q & 3 at
+// counter (q >> 2, 0, chain, 2), q = site >> 5, site = y L + x.
+__global__ void init_lattice_kernel(const DevJob j, const int start) {
+  const long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  const long long total = static_cast<long long>(j.p) * j.L * j.wd;
+  if (idx >= total) return;
+  const int w = static_cast<int>(idx % j.wd);
+  const long long cy = idx / j.wd;
+  const int y = static_cast<int>(cy % j.L);
+  const uint32_t c = static_cast<uint32_t>(cy / j.L);
+  const int x0 = 32 * w, x1 = min(j.L, x0 + 32);
+  uint32_t word = 0u;
+  if (start == 0) {
+    word = (x1 - x0 == 32) ? 0xFFFFFFFFu : ((1u << (x1 - x0)) - 1u);
+  } else {
+    uint32_t cached = 0xFFFFFFFFu, R = 0u;
+    for (int x = x0; x < x1; ++x) {
+      const uint32_t site = static_cast<uint32_t>(y * j.L + x);
+      const uint32_t q = site >> 5;
+      if (q != cached) {
+        const uint4 v = philox4x32_10(make_uint4(q >> 2, 0u, c, kTagInit), j.key0, j.key1);
+        R = uint4_word(v, q & 3u);
+        cached = q;
+      }
+      word |= ((R >> (site & 31u)) & 1u) << (x - x0);
+    }
+  }
+  j.spins[idx] = word;
+}
+
+__device__ __forceinline__ uint32_t site_bit(const uint32_t* lat, int wd, int L, int x, int y) {
+  x = (x + L) % L;
+  y = (y + L) % L;
+  return (lat[y * wd + (x >> 5)] >> (x & 31)) & 1u;
+}
+
+// Level m = (E + 2N)/4 of each chain's lattice, E = -sum s (s_right + s_down).
+__global__ void levels_kernel(const DevJob j) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= j.p) return;
+  const uint32_t* lat = j.spins + static_cast<size_t>(c) * j.L * j.wd;
+  int E = 0;
+  for (int y = 0; y < j.L; ++y)
+    for (int x = 0; x < j.L; ++x) {
+      const int s = site_bit(lat, j.wd, j.L, x, y) ? 1 : -1;
+      const int r = site_bit(lat, j.wd, j.L, x + 1, y) ? 1 : -1;
+      const int d = site_bit(lat, j.wd, j.L, x, y + 1) ? 1 : -1;
+      E -= s * (r + d);
+    }
+  j.m[c] = (E + 2 * j.N) / 4;
+}
+
+// T[a][m] = thr(W[m + a - 2] - W[m]); moves outside [0, N] never occur.
+__global__ void table_kernel(const DevJob j) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 5 * j.np1) return;
+  const int a = idx / j.np1, m = idx % j.np1;
+  const int mp = m + a - 2;
+  j.T[idx] = (mp < 0 || mp > j.N) ? 0u : threshold_det(__dsub_rn(j.W[mp], j.W[m]));
+}
+
+// Eq. (new_weight) in logarithms: W -= ln h where h > 0; h cleared.
+__global__ void weights_kernel(const DevJob j) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= j.np1) return;
+  const long long h = j.h[m];
+  if (h > 0) j.W[m] = __dsub_rn(j.W[m], log_det(static_cast<double>(h)));
+  j.h[m] = 0;
+}
+
+// Joint thresholds for each listed chain's input level x: tj[i][m] = thr(W[m] - W[x]).
+__global__ void tj_kernel(const DevJob j, const int32_t* __restrict__ list, const int n) {
+  const long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (idx >= static_cast<long long>(n) * j.np1) return;
+  const int q = static_cast<int>(idx / j.np1), m = static_cast<int>(idx % j.np1);
+  const int i = list ? list[q] : q;
+  const int x = j.xused[i];
+  if (x < 0) return;
+  j.tj[static_cast<size_t>(i) * j.np1 + m] = threshold_det(__dsub_rn(j.W[m], j.W[x]));
+}
+
+// Speculated inputs: chain i is assumed to receive the last configuration of
+// chain i-1 (chain 0 receives the carry from the previous round, or nothing
+// in the job's first round).
+__global__ void spec_inputs_kernel(const DevJob j) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= j.p) return;
+  int x;
+  if (i == 0)
+    x = j.stats[kStatCarryValid] ? static_cast<int>(j.stats[kStatCarry]) : -1;
+  else
+    x = j.m[i - 1];
+  j.xused[i] = x;
+}
+
+// Segmented scan and histogram: kept length of chain i is M - k_i + 1 (0 if
+// nothing is kept); offsets are the exclusive scan; h += hgen - dpre.
+__global__ void __launch_bounds__(1024) finalize_kernel(const DevJob j, const int64_t S) {
+  __shared__ long long s_tmp[1024];
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int64_t M = S * j.N;
+  for (int m = t; m < j.np1; m += nt) {
+    j.h[m] += static_cast<long long>(j.hgen[m] - j.dpre[m]);
+    j.hgen[m] = 0ull;
+    j.dpre[m] = 0ull;
+  }
+  const int per = (j.p + nt - 1) / nt;
+  const int lo = min(j.p, t * per), hi = min(j.p, lo + per);
+  long long sum = 0, rej = 0;
+  for (int i = lo; i < hi; ++i) {
+    const int64_t k = j.k[i];
+    sum += k > 0 ? (M - k + 1) : 0;
+    rej += k > 0 ? 0 : 1;
+  }
+  s_tmp[t] = sum;
+  __syncthreads();
+  for (int off = 1; off < nt; off <<= 1) {
+    const long long v = (t >= off) ? s_tmp[t - off] : 0;
+    __syncthreads();
+    s_tmp[t] += v;
+    __syncthreads();
+  }
+  long long run = s_tmp[t] - sum;
+  for (int i = lo; i < hi; ++i) {
+    j.offsets[i] = run;
+    const int64_t k = j.k[i];
+    run += k > 0 ? (M - k + 1) : 0;
+  }
+  if (t == nt - 1) {
+    j.stats[kStatJoined] = s_tmp[t];
+    j.stats[kStatJoinedTotal] += s_tmp[t];
+  }
+  __syncthreads();
+  s_tmp[t] = rej;
+  __syncthreads();
+  if (t == 0) {
+    long long r = 0;
+    for (int q = 0; q < nt; ++q) r += s_tmp[q];
+    j.stats[kStatRejected] = r;
+  }
+}
+
+// Control experiment (no detailed balance at the joints): keep everything.
+__global__ void naive_kernel(const DevJob j) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < j.p) {
+    j.k[i] = 1;
+    j.kspec[i] = 1;
+    j.xused[i] = -1;
+  }
+  if (i == 0) {
+    j.stats[kStatCarry] = j.m[j.p - 1];
+    j.stats[kStatCarryValid] = 1;
+    j.stats[kStatMismatch] = 0;
+    j.stats[kStatPasses] = 0;
+  }
+}
+
+__global__ void clear_stats_kernel(const DevJob j) {
+  if (threadIdx.x == 0) j.stats[kStatSearched] = 0;
+}
+
+// ------------------------------------------------------------------ host side
+size_t gen_smem_bytes(int L, const LaunchShape& s, bool* table_in_smem) {
+  const bool ts = table_fits(L, s, true);
+  if (table_in_smem) *table_in_smem = ts;
+  return plan_bytes(L, s, ts, true);
+}
+
+bool shape_supported(int L, const LaunchShape& s) {
+  if (L < 4 || L > 128 || (L % 4) != 0) return false;
+  if (s.cpw < 1 || s.cpw > 32 || s.wpb < 1 || s.wpb > 4) return false;
+  if (s.placement == kPlaceReg && L > 32) return false;
+  if (s.placement != kPlaceReg && s.placement != kPlaceSmem) return false;
+  return plan_bytes(L, s, false, true) <= kMaxSmem;
+}
+
+LaunchShape default_shape(int L, int p, int num_sms) {
+  LaunchShape s;
+  s.placement = (L <= 32) ? kPlaceReg : kPlaceSmem;
+  s.wpb = 4;
+  const int warps = std::max(1, num_sms) * 4;  // one warp per SM sub-partition
+  s.cpw = std::min(32, std::max(1, (p + warps - 1) / warps));
+  while (s.wpb > 1 && !shape_supported(L, s)) s.wpb >>= 1;
+  while (s.cpw > 1 && !shape_supported(L, s)) s.cpw >>= 1;
+  return s;
+}
+
+cudaError_t join_prelude(const DevJob& j, cudaStream_t st) {
+  spec_inputs_kernel<<<blocks_for(j.p, 256), 256, 0, st>>>(j);
+  clear_stats_kernel<<<1, 32, 0, st>>>(j);
+  tj_kernel<<<blocks_for(static_cast<long long>(j.p) * j.np1, 256), 256, 0, st>>>(j, nullptr, j.p);
+  launches_add(3);
+  return cudaGetLastError();
+}
+
+cudaError_t join_finalize(const DevJob& j, int64_t S, cudaStream_t st) {
+  finalize_kernel<<<1, 1024, 0, st>>>(j, S);
+  launches_add(1);
+  return cudaGetLastError();
+}
+
+static cudaError_t dispatch(const DevJob& j, const LaunchShape& s, bool gen, uint64_t t0, int64_t S, bool trace,
+                            uint32_t r, cudaStream_t st) {
+  if (s.placement == kPlaceReg) {
+    if (j.L <= 16) return chain_kernels_reg_a(j, s, gen, t0, S, trace, r, st);
+    if (j.L <= 28) return chain_kernels_reg_b(j, s, gen, t0, S, trace, r, st);
+    return chain_kernels_reg_c(j, s, gen, t0, S, trace, r, st);
+  }
+  switch (j.wd) {
+    case 1: return chain_kernels_smem_1(j, s, gen, t0, S, trace, r, st);
+    case 2: return chain_kernels_smem_2(j, s, gen, t0, S, trace, r, st);
+    case 3: return chain_kernels_smem_3(j, s, gen, t0, S, trace, r, st);
+    case 4: return chain_kernels_smem_4(j, s, gen, t0, S, trace, r, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t k_generate(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S, bool trace, cudaStream_t st) {
+  return dispatch(j, s, true, t0, S, trace, 0u, st);
+}
+
+cudaError_t k_join(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S, uint32_t r, bool naive,
+                   cudaStream_t st) {
+  if (naive) {
+    naive_kernel<<<blocks_for(j.p, 256), 256, 0, st>>>(j);
+    finalize_kernel<<<1, 1024, 0, st>>>(j, S);
+    launches_add(2);
+    return cudaGetLastError();
+  }
+  return dispatch(j, s, false, t0, S, false, r, st);
+}
+
+cudaError_t k_init_lattice(const DevJob& j, int start, cudaStream_t st) {
+  const long long n = static_cast<long long>(j.p) * j.L * j.wd;
+  init_lattice_kernel<<<blocks_for(n, 256), 256, 0, st>>>(j, start);
+  launches_add(1);
+  return cudaGetLastError();
+}
+
+cudaError_t k_levels(const DevJob& j, cudaStream_t st) {
+  levels_kernel<<<blocks_for(j.p, 128), 128, 0, st>>>(j);
+  launches_add(1);
+  return cudaGetLastError();
+}
+
+cudaError_t k_build_table(const DevJob& j, cudaStream_t st) {
+  table_kernel<<<blocks_for(5ll * j.np1, 256), 256, 0, st>>>(j);
+  launches_add(1);
+  return cudaGetLastError();
+}
+
+cudaError_t k_update_weights(const DevJob& j, cudaStream_t st) {
+  weights_kernel<<<blocks_for(j.np1, 256), 256, 0, st>>>(j);
+  launches_add(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return k_build_table(j, st);
+}
+
+}  // namespace mcgpu

@@ -1,0 +1,58 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/*.h declares (no compute calls: no GPU here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_0812_2964_gb300 as mc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(mc_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return mc.build()
+
+
+def test_header_declares_the_core_calls():
+    d = _declared()
+    for name in ("mc_init", "mc_run_sweeps", "mc_join", "mc_histogram", "mc_update_weights"):
+        assert name in d
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header(libpath):
+    for n in _declared():
+        assert hasattr(mc, n), n
+
+
+def test_no_gpu_call_without_device(libpath):
+    # loading is fine; the launch counter is a pure host query
+    assert mc.mc_kernel_launches() >= 0
+    assert isinstance(mc.mc_last_error(), str)
+
+
+def test_init_rejects_bad_arguments(libpath):
+    # argument checks happen before any CUDA call
+    for L, p, start in [(3, 4, 0), (6, 4, 0), (132, 4, 0), (8, 0, 0), (8, 4, 2)]:
+        with pytest.raises(mc.McError) as e:
+            mc.mc_init(L, p, 1, start)
+        assert e.value.code == mc.MC_EINVAL

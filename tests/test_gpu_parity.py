@@ -1,0 +1,176 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Bit-exact: spins, energies, per-sweep traces, first kept samples k_i, joined
+lengths, carries, histograms, thresholds.  W after each update: identical
+bits expected (same IEEE operations in the same order); the required bound
+is 1e-12 absolute.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_0812_2964_gb300 as mc
+from paper_0812_2964_gb300.workloads import WORKLOADS, random_weights
+
+pytestmark = pytest.mark.gpu
+
+W_TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    mc.build()
+
+
+def _compare_state(g, o, L):
+    N = L * L
+    assert np.array_equal(g.spin_words, oracle.pack_spins(o.spins))
+    assert np.array_equal(g.energies, 4 * o.levels - 2 * N)
+
+
+def _compare_weights(g, o):
+    Wg, Wo = g.weights, o.weights
+    assert np.abs(Wg - Wo).max() <= W_TOL
+    assert np.array_equal(Wg, Wo)            # same operations, same order: same bits
+    assert np.array_equal(g.table, o.table)
+
+
+def _run_parity(L, p, S, iters, start, seed, weights=None, shape=None, M_total=0):
+    N = L * L
+    g = mc.Job(L, p, seed, start)
+    if shape is not None:
+        g.set_launch_shape(*shape)
+    g.set_trace(True)
+    o = oracle.Job(L, p, seed, start)
+    if weights is not None:
+        g.weights = weights
+        o.weights = weights
+    _compare_state(g, o, L)
+    _compare_weights(g, o)
+    mism = 0
+    for it in range(iters):
+        tot_g = tot_o = 0
+        while True:
+            g.run_sweeps(S)
+            o.run_round(S, nthreads=8)
+            _compare_state(g, o, L)
+            assert np.array_equal(g.trace, 4 * o.trace - 2 * N)
+            jg, jo = g.join(), o.join()
+            assert jg == jo
+            assert np.array_equal(g.k, o.k)
+            info = g.info()
+            mism += info["last_mismatch"]
+            assert info["carry_valid"] == 1
+            assert info["carry_energy"] == 4 * o.carry - 2 * N
+            hg = g.hist
+            assert np.array_equal(hg, o.hist)
+            tot_g += jg
+            tot_o += jo
+            if tot_o >= M_total:
+                break
+        g.update_weights()
+        o.update_weights()
+        _compare_weights(g, o)
+    return g, o, mism
+
+
+@pytest.mark.parametrize("L,p,S,iters,start", [
+    (4, 5, 3, 4, 1), (8, 37, 7, 4, 1), (12, 33, 5, 3, 1), (16, 100, 4, 3, 1), (20, 32, 2, 4, 1),
+    (24, 50, 3, 3, 1), (28, 17, 2, 3, 1), (32, 130, 3, 4, 1), (36, 40, 2, 3, 1), (48, 33, 2, 3, 1),
+    (64, 20, 2, 3, 1), (100, 9, 1, 3, 1), (128, 6, 1, 2, 1), (32, 3, 2, 3, 0),
+])
+def test_weight_iterations_bit_exact(L, p, S, iters, start):
+    _run_parity(L, p, S, iters, start, seed=1000 + L)
+
+
+@pytest.mark.parametrize("L,p,S", [(8, 40, 5), (32, 70, 2), (64, 12, 1)])
+def test_rugged_weight_rejections_and_resolution(L, p, S):
+    # a rough weight makes many chains keep nothing, so speculated joint
+    # inputs are often wrong and the resolution passes must fix them
+    W = random_weights(L, seed=L, scale=12.0)
+    g, o, mism = _run_parity(L, p, S, 3, 1, seed=77, weights=W)
+    assert mism > 0
+
+
+@pytest.mark.parametrize("shape", [(0, 27, 4), (0, 32, 1), (0, 5, 3), (1, 8, 2), (1, 32, 4), (1, 1, 1)])
+def test_launch_shape_does_not_change_results(shape):
+    _run_parity(32, 130, 2, 3, 1, seed=5, weights=random_weights(32, 3, 4.0), shape=shape)
+
+
+@pytest.mark.parametrize("shape", [(1, 3, 4), (1, 16, 1)])
+def test_launch_shape_large_lattice(shape):
+    _run_parity(64, 21, 1, 2, 1, seed=6, shape=shape)
+
+
+def test_rounds_until_M_total():
+    _run_parity(16, 20, 2, 3, 1, seed=9, M_total=int(2.5 * 20 * 2 * 256))
+
+
+def test_naive_join_matches_oracle():
+    L, p, S = 16, 24, 3
+    g = mc.Job(L, p, 4, 1)
+    o = oracle.Job(L, p, 4, 1)
+    W = random_weights(L, 8, 5.0)
+    g.weights = W
+    o.weights = W
+    for _ in range(2):
+        g.run_sweeps(S)
+        o.run_round(S)
+        assert g.join_naive() == o.join_naive() == p * S * L * L
+        assert np.array_equal(g.hist, o.hist)
+        assert (g.k == 1).all()
+        g.update_weights()
+        o.update_weights()
+        _compare_weights(g, o)
+
+
+def test_config_L8_p64_all_iterations():
+    w = WORKLOADS["L8_p64"]
+    _run_parity(w.L, w.chains, w.sweeps, w.iterations, w.start, w.seed)
+
+
+def test_offsets_are_exclusive_scan_of_kept_lengths():
+    L, p, S = 8, 50, 3
+    g = mc.Job(L, p, 12, 1)
+    g.weights = random_weights(L, 1, 8.0)
+    g.run_sweeps(S)
+    joined = g.join()
+    k, off = g.k, g.offsets
+    M = S * L * L
+    kept = np.where(k > 0, M - k + 1, 0)
+    assert joined == kept.sum() == g.hist.sum()
+    assert np.array_equal(off, np.concatenate([[0], np.cumsum(kept)[:-1]]))
+
+
+def test_call_order_and_argument_errors():
+    g = mc.Job(8, 4, 1, 1)
+    with pytest.raises(mc.McError) as e:
+        g.join()
+    assert e.value.code == mc.MC_ESTATE
+    g.run_sweeps(1)
+    with pytest.raises(mc.McError) as e:
+        g.run_sweeps(1)
+    assert e.value.code == mc.MC_ESTATE
+    with pytest.raises(mc.McError) as e:
+        g.update_weights()
+    assert e.value.code == mc.MC_ESTATE
+    g.join()
+    with pytest.raises(mc.McError) as e:
+        mc.mc_set_weights(g.h, np.zeros(5))
+    assert e.value.code == mc.MC_EINVAL
+    with pytest.raises(mc.McError) as e:
+        g.set_launch_shape(0, 33, 1)
+    assert e.value.code == mc.MC_EINVAL
+    with pytest.raises(mc.McError) as e:
+        mc.mc_run_sweeps(g.h, 0)
+    assert e.value.code == mc.MC_EINVAL
+
+
+def test_set_spins_roundtrip_and_energy():
+    L, p = 48, 3
+    g = mc.Job(L, p, 2, 0)
+    rng = np.random.default_rng(0)
+    s = rng.choice(np.array([-1, 1], np.int8), size=(p, L, L))
+    g.spin_words = oracle.pack_spins(s)
+    assert np.array_equal(g.spin_words, oracle.pack_spins(s))
+    assert list(g.energies) == [oracle.energy(s[c]) for c in range(p)]
