@@ -141,6 +141,7 @@ int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
       (rc = dalloc(j, &d.k, n_chains)) || (rc = dalloc(j, &d.kspec, n_chains)) ||
       (rc = dalloc(j, &d.xused, n_chains)) || (rc = dalloc(j, &d.tj, static_cast<size_t>(n_chains) * np1)) ||
       (rc = dalloc(j, &d.offsets, n_chains)) || (rc = dalloc(j, &d.work, n_chains)) ||
+      (rc = dalloc(j, &d.lastacc, n_chains)) ||
       (rc = dalloc(j, &d.stats, mcgpu::kStatCount))) {
     free_all(j);
     delete j;

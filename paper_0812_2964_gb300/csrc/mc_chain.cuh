@@ -23,19 +23,97 @@
 
 namespace mcgpu {
 
-template <int WD>
-struct RowInputs {
-  uint32_t up[WD], dn[WD];
+// Uniforms of the next 32-site word, computed one word ahead so that the
+// eight independent Philox blocks fill the latency gaps of the current
+// word's serial Metropolis chain.  blk is the Philox block index of the
+// first attempt after the prefetched word.
+struct Prefetch {
+  uint32_t U[32];
+  uint64_t blk;
 };
 
-// Sweep one row in place.  blk is the Philox block index of the next
-// attempt (the row starts on a block boundary since L % 4 == 0).
+__device__ __forceinline__ void philox_fill(uint32_t (&U)[32], const int n, const uint64_t blk, const uint32_t chain,
+                                            const uint32_t k0, const uint32_t k1) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (4 * q < n) {
+      const uint64_t b = blk + static_cast<uint64_t>(q);
+      const uint4 r =
+          philox4x32_10(make_uint4(static_cast<uint32_t>(b), static_cast<uint32_t>(b >> 32), chain, kTagFlip), k0, k1);
+      U[4 * q + 0] = r.x;
+      U[4 * q + 1] = r.y;
+      U[4 * q + 2] = r.z;
+      U[4 * q + 3] = r.w;
+    }
+  }
+}
+
+// Start a chain's attempt stream at attempt t0 (a multiple of 4).
+template <int WD>
+__device__ __forceinline__ void prefetch_init(Prefetch& pf, const int L, const uint64_t t0, const uint32_t chain,
+                                              const uint32_t k0, const uint32_t k1) {
+  const int lw = L - 32 * (WD - 1);
+  const int n0 = (WD == 1) ? lw : 32;
+  philox_fill(pf.U, n0, t0 >> 2, chain, k0, k1);
+  pf.blk = (t0 >> 2) + static_cast<uint64_t>(n0 / 4);
+}
+
+// Shared-memory reduction at a byte offset (no return value, no branch).
+// (A host compiler -- used to check this logic on the CPU -- gets a plain add.)
+__device__ __forceinline__ void red_shared_add(uint32_t* base, const int byte_off, const uint32_t v) {
+#ifdef __CUDACC__
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(base)) + static_cast<uint32_t>(byte_off);
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v));
+#else
+  base[byte_off >> 2] += v;
+#endif
+}
+
+// Byte permute (PTX prmt, generic mode): selector nibble bit 3 set means
+// "replicate the sign of the selected byte".
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t sel) {
+#ifdef __CUDACC__
+  uint32_t d;
+  asm("prmt.b32 %0, %1, 0, %2;" : "=r"(d) : "r"(a), "r"(sel));
+  return d;
+#else
+  uint32_t d = 0;
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t s = (sel >> (4 * i)) & 0xFu;
+    const uint32_t src = (s & 7u) < 4 ? ((a >> (8 * (s & 7u))) & 0xFFu) : 0u;
+    const uint32_t v = (s & 8u) ? ((src & 0x80u) ? 0xFFu : 0u) : src;
+    d |= v << (8 * i);
+  }
+  return d;
+#endif
+}
+
+// Selector of byte k, sign-extended to 32 bits.
+__device__ __forceinline__ constexpr uint32_t sign_sel(uint32_t k) {
+  return k | ((k | 8u) << 4) | ((k | 8u) << 8) | ((k | 8u) << 12);
+}
+
+// Spread the 4 bits of n (0..15) into the low bits of 4 bytes.
+__device__ __forceinline__ uint32_t spread4(uint32_t n) { return (n * 0x00204081u) & 0x01010101u; }
+
+// Sweep one row in place.  The row starts on a Philox block boundary
+// (L % 4 == 0); pf holds the uniforms of the row's first word.
+//
+// Per site b the move is to level m + a - 2 with a = as + (el ^ f): as counts
+// the up/down/right neighbours aligned with the spin, el is 1 if the left
+// neighbour was aligned before its own attempt, f is that attempt's flip.
+// Per group of 4 sites the bytes A0 (4 a for f = 0) and D (4 a(f=1) - 4 a(f=0)
+// = +-4, signed) are packed once; a site then needs one byte permute each.
+// Levels are kept as byte offsets m4 = 4 m, so that table and histogram
+// addresses are plain register + constant.  The thresholds of site b+1 under
+// both flips of site b are loaded while site b is resolved, from the level
+// before site b.  Accepted flips accumulate in a mask applied at the word's
+// end; the left neighbour's flip is tracked in f.
 template <int WD, class Hook>
 __device__ __forceinline__ void sweep_row(uint32_t (&cur)[WD], const uint32_t (&up)[WD],
                                           const uint32_t (&dn)[WD], const int L, int& m,
-                                          const uint32_t* __restrict__ T, const int np1,
-                                          uint64_t& blk, const uint32_t chain, const uint32_t k0,
-                                          const uint32_t k1, Hook& hook) {
+                                          const uint32_t* __restrict__ T, const int np1, Prefetch& pf,
+                                          const uint32_t chain, const uint32_t k0, const uint32_t k1, Hook& hook) {
   const int lw = L - 32 * (WD - 1);  // sites in the last word of the row
   uint32_t s0[WD], s1[WD], el[WD], eu[WD], ed[WD], er[WD];
 #pragma unroll
@@ -52,61 +130,94 @@ __device__ __forceinline__ void sweep_row(uint32_t (&cur)[WD], const uint32_t (&
     s0[w] = eu[w] ^ ed[w] ^ er[w];                         // sum bit
     s1[w] = (eu[w] & ed[w]) | (er[w] & (eu[w] ^ ed[w]));  // carry bit
   }
+  int m4 = 4 * m;
   uint32_t f = 0u, f0 = 0u;  // flip of the previous site / of site 0
-  uint4 rnd = make_uint4(0u, 0u, 0u, 0u);
+  const char* Tb = reinterpret_cast<const char*>(T);
 #pragma unroll
   for (int w = 0; w < WD; ++w) {
     const int nb = (w + 1 < WD) ? 32 : lw;
+    uint32_t u[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) u[i] = pf.U[i];
+    const int nb_next = (w + 1 < WD) ? ((w + 2 < WD) ? 32 : lw) : ((WD == 1) ? lw : 32);
+    philox_fill(pf.U, nb_next, pf.blk, chain, k0, k1);
+    pf.blk += static_cast<uint64_t>(nb_next / 4);
+    // packed per-site bytes
+    uint32_t A0[8], D[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (4 * q < nb) {
+        const uint32_t b0 = spread4((s0[w] >> (4 * q)) & 0xFu);
+        const uint32_t b1 = spread4((s1[w] >> (4 * q)) & 0xFu);
+        const uint32_t b2 = spread4((el[w] >> (4 * q)) & 0xFu);
+        A0[q] = 4u * b0 + 8u * b1 + 4u * b2;     // 4 (s0 + 2 s1 + el), no carries
+        D[q] = 0x04040404u + 0xF8u * b2;         // +4 (el = 0) or -4 (el = 1) as signed bytes
+      }
+    }
+    uint32_t F = 0u;  // flips of this word
+    uint32_t t0, t1;
+    {
+      // first site of the word: state before it is known, one load
+      const int a4 = static_cast<int>(prmt(A0[0], 0x4440u)) + static_cast<int>(f) * static_cast<int>(prmt(D[0], 0x8880u));
+      t0 = t1 = *reinterpret_cast<const uint32_t*>(Tb + a4 * np1 + m4);
+    }
 #pragma unroll
     for (int b = 0; b < 32; ++b) {
       if (b < nb) {
-        if ((b & 3) == 0) {
-          rnd = philox4x32_10(make_uint4(static_cast<uint32_t>(blk), static_cast<uint32_t>(blk >> 32),
-                                         chain, kTagFlip),
-                              k0, k1);
-          ++blk;
-        }
-        const uint32_t u = (b & 3) == 0 ? rnd.x : ((b & 3) == 1 ? rnd.y : ((b & 3) == 2 ? rnd.z : rnd.w));
-        int a;
-        if (w == WD - 1 && b == nb - 1) {
-          a = static_cast<int>(((eu[w] >> b) & 1u) + ((ed[w] >> b) & 1u) + (((er[w] >> b) & 1u) ^ f0) +
-                               (((el[w] >> b) & 1u) ^ f));
+        const bool last = (w == WD - 1 && b == nb - 1);
+        const uint32_t selz = 0x4440u | static_cast<uint32_t>(b & 3);
+        const uint32_t sels = sign_sel(static_cast<uint32_t>(b & 3));
+        int a0m, d4;
+        if (last) {
+          const uint32_t elb = (el[w] >> b) & 1u;
+          a0m = 4 * static_cast<int>(((eu[w] >> b) & 1u) + ((ed[w] >> b) & 1u) + (((er[w] >> b) & 1u) ^ f0) + elb);
+          d4 = elb ? -4 : 4;
         } else {
-          a = static_cast<int>(((s0[w] >> b) & 1u) + 2u * ((s1[w] >> b) & 1u) + (((el[w] >> b) & 1u) ^ f));
+          a0m = static_cast<int>(prmt(A0[b >> 2], selz));
+          d4 = static_cast<int>(prmt(D[b >> 2], sels));
         }
-        const uint32_t thr = T[a * np1 + m];
-        const uint32_t acc = (u <= thr) ? 1u : 0u;
-        const int mold = m;
-        if (acc) {
-          cur[w] ^= (1u << b);
-          m += a - 2;
+        const int a4 = a0m + static_cast<int>(f) * d4;   // 4 a for this site
+        const int dl = a4 - 8;                            // level change (x4) if it flips
+        const uint32_t thr = f ? t1 : t0;
+        const uint32_t acc = (u[b] <= thr) ? 1u : 0u;
+        if (b + 1 < nb) {
+          const bool nlast = (w == WD - 1 && b + 1 == nb - 1);
+          int na0, nd4;
+          if (nlast) {
+            const uint32_t ff0 = (w == 0 && b == 0) ? acc : f0;
+            const uint32_t eln = (el[w] >> (b + 1)) & 1u;
+            na0 = 4 * static_cast<int>(((eu[w] >> (b + 1)) & 1u) + ((ed[w] >> (b + 1)) & 1u) +
+                                      (((er[w] >> (b + 1)) & 1u) ^ ff0) + eln);
+            nd4 = eln ? -4 : 4;
+          } else {
+            na0 = static_cast<int>(prmt(A0[(b + 1) >> 2], 0x4440u | static_cast<uint32_t>((b + 1) & 3)));
+            nd4 = static_cast<int>(prmt(D[(b + 1) >> 2], sign_sel(static_cast<uint32_t>((b + 1) & 3))));
+          }
+          const int off0 = na0 * np1 + m4;                 // site b not flipped
+          t0 = *reinterpret_cast<const uint32_t*>(Tb + off0);
+          t1 = *reinterpret_cast<const uint32_t*>(Tb + off0 + nd4 * np1 + dl);   // site b flipped
         }
+        F += acc << b;
+        m4 += static_cast<int>(acc) * dl;
         f = acc;
         if (w == 0 && b == 0) f0 = acc;
-        hook.sample(mold, m);
+        hook.sample(m4);
       }
     }
+    cur[w] ^= F;
   }
+  m = m4 >> 2;
 }
 
 // ------------------------------------------------------------------ hooks
-// Generation: dwell-time histogram in a warp-private u32 shared-memory
-// array (one atomic per change of level, adding the run length).
+// Generation: every sample adds 1 to its level's u32 counter in the block's
+// shared-memory histogram (one reduction, no branch).  Hooks receive the
+// level of the sample as m4 = 4 m (a byte offset into u32 arrays).
 struct GenHook {
   uint32_t* hist;
-  uint32_t run;
-  __device__ __forceinline__ void sample(int mold, int m) {
-    if (m != mold) {
-      atomicAdd(&hist[mold], run);
-      run = 1u;
-    } else {
-      ++run;
-    }
-  }
-  __device__ __forceinline__ void flush(int m) {
-    if (run) atomicAdd(&hist[m], run);
-    run = 0u;
-  }
+  uint32_t run;  // unused; kept for a uniform hook interface
+  __device__ __forceinline__ void sample(int m4) { red_shared_add(hist, m4, 1u); }
+  __device__ __forceinline__ void flush(int) {}
 };
 
 // Joint search (Sec. 2 step 4): for samples k = 1..M of the chain (the
@@ -126,8 +237,9 @@ struct SearchHook {
   int cur_level;
   uint32_t run;
   bool done;
-  __device__ __forceinline__ void sample(int /*mold*/, int m) {
+  __device__ __forceinline__ void sample(int m4) {
     if (done) return;
+    const int m = m4 >> 2;
     ++k;
     const uint64_t q = static_cast<uint64_t>(k - 1);
     if ((q & 3u) == 0u)
@@ -167,8 +279,9 @@ struct CorrectHook {
   int cur_level;
   uint32_t run;
   bool done;
-  __device__ __forceinline__ void sample(int /*mold*/, int m) {
+  __device__ __forceinline__ void sample(int m4) {
     if (done) return;
+    const int m = m4 >> 2;
     ++k;
     if (k >= hi) {
       flush();

@@ -30,14 +30,14 @@ struct RegRunner {
     for (int y = 0; y < L; ++y) g[y] = R[y];
   }
   template <bool EARLY, class Hook>
-  __device__ __forceinline__ void sweep(int& m, uint64_t& blk, const uint32_t* __restrict__ T, int np1,
+  __device__ __forceinline__ void sweep(int& m, Prefetch& pf, const uint32_t* __restrict__ T, int np1,
                                         uint32_t chain, uint32_t k0, uint32_t k1, Hook& hk) {
 #pragma unroll 1
     for (int y = 0; y < L; ++y) {
       uint32_t cur[1] = {R[0]};
       const uint32_t up[1] = {R[L - 1]};
       const uint32_t dn[1] = {R[1]};
-      sweep_row<1>(cur, up, dn, L, m, T, np1, blk, chain, k0, k1, hk);
+      sweep_row<1>(cur, up, dn, L, m, T, np1, pf, chain, k0, k1, hk);
 #pragma unroll
       for (int i = 0; i < L - 1; ++i) R[i] = R[i + 1];
       R[L - 1] = cur[0];
@@ -48,8 +48,9 @@ struct RegRunner {
   }
 };
 
-template <int WD>
+template <int WD_>
 struct SmemRunner {
+  static constexpr int WD = WD_;
   uint32_t* lat;  // this chain's column
   int stride, L;
   __device__ __forceinline__ void load(const uint32_t* __restrict__ g) {
@@ -59,7 +60,7 @@ struct SmemRunner {
     for (int i = 0; i < L * WD; ++i) g[i] = lat[i * stride];
   }
   template <bool EARLY, class Hook>
-  __device__ __forceinline__ void sweep(int& m, uint64_t& blk, const uint32_t* __restrict__ T, int np1,
+  __device__ __forceinline__ void sweep(int& m, Prefetch& pf, const uint32_t* __restrict__ T, int np1,
                                         uint32_t chain, uint32_t k0, uint32_t k1, Hook& hk) {
 #pragma unroll 1
     for (int y = 0; y < L; ++y) {
@@ -71,7 +72,7 @@ struct SmemRunner {
         up[w] = lat[(ym * WD + w) * stride];
         dn[w] = lat[(yp * WD + w) * stride];
       }
-      sweep_row<WD>(cur, up, dn, L, m, T, np1, blk, chain, k0, k1, hk);
+      sweep_row<WD>(cur, up, dn, L, m, T, np1, pf, chain, k0, k1, hk);
 #pragma unroll
       for (int w = 0; w < WD; ++w) lat[(y * WD + w) * stride] = cur[w];
       if constexpr (EARLY) {
@@ -157,19 +158,21 @@ __global__ void __launch_bounds__(128) gen_kernel(const DevJob j, const int cpw,
   auto run = Factory::make(b, j.L);
   __syncthreads();
   int m = 0;
-  uint64_t blk = t0 >> 2;
+  Prefetch pf;
   GenHook hk{b.hist, 0u};
   if (b.active) {
     run.load(j.spins + static_cast<size_t>(b.chain) * j.L * j.wd);
     m = j.m[b.chain];
+    prefetch_init<decltype(run)::WD>(pf, j.L, t0, static_cast<uint32_t>(b.chain), j.key0, j.key1);
   }
   for (int64_t s = 0; s < S; ++s) {
     if (b.active) {
-      run.template sweep<false>(m, blk, b.T, j.np1, static_cast<uint32_t>(b.chain), j.key0, j.key1, hk);
+      run.template sweep<false>(m, pf, b.T, j.np1, static_cast<uint32_t>(b.chain), j.key0, j.key1, hk);
       if (do_trace) j.trace[s * j.p + b.chain] = 4 * m - 2 * j.N;
     }
     if (flushF > 0 && (s + 1) % flushF == 0 && s + 1 < S) {
       if (b.active) hk.flush(m);
+      asm volatile("" ::: "memory");
       __syncthreads();
       for (int i = threadIdx.x; i < j.np1; i += blockDim.x) {
         const uint32_t v = b.hist[i];
@@ -186,6 +189,7 @@ __global__ void __launch_bounds__(128) gen_kernel(const DevJob j, const int cpw,
     run.store(j.spins + static_cast<size_t>(b.chain) * j.L * j.wd);
     j.m[b.chain] = m;
   }
+  asm volatile("" ::: "memory");
   __syncthreads();
   for (int i = threadIdx.x; i < j.np1; i += blockDim.x) {
     const uint32_t v = b.hist[i];
@@ -202,9 +206,10 @@ __device__ __forceinline__ void replay_chain(const DevJob& j, const BlockCtx& b,
   auto run = Factory::make(b, j.L);
   run.load(j.spins0 + static_cast<size_t>(i) * j.L * j.wd);
   int m = j.m0[i];
-  uint64_t blk = t0 >> 2;
+  Prefetch pf;
+  prefetch_init<decltype(run)::WD>(pf, j.L, t0, static_cast<uint32_t>(i), j.key0, j.key1);
   for (int64_t s = 0; s < S && !hk.done; ++s)
-    run.template sweep<true>(m, blk, b.T, j.np1, static_cast<uint32_t>(i), j.key0, j.key1, hk);
+    run.template sweep<true>(m, pf, b.T, j.np1, static_cast<uint32_t>(i), j.key0, j.key1, hk);
 }
 
 // Speculative joint search (step 4 with input = last level of chain i-1):
@@ -244,12 +249,10 @@ __global__ void __launch_bounds__(128) spec_kernel(const DevJob j, const int cpw
   j.kspec[i] = k;
 }
 
-// Block-wide inclusive max-scan of int values (one value per element, p
-// elements, each thread a contiguous range), used for "last accepted chain
-// before i".
-static __device__ void block_last_accepted(const DevJob& j, int* s_tmp) {
-  // s_tmp: blockDim.x ints.  Writes into j.work[i] the index of the last
-  // chain < i whose k > 0 (or -1).
+// Block-wide scan: out[i] = index of the last chain before i whose k > 0
+// (or -1).  Each thread takes a contiguous range of chains; s_tmp holds
+// blockDim.x ints.
+__device__ __forceinline__ void block_last_accepted(const DevJob& j, int* s_tmp, int32_t* out) {
   const int t = threadIdx.x, nt = blockDim.x;
   const int per = (j.p + nt - 1) / nt;
   const int lo = min(j.p, t * per), hi = min(j.p, lo + per);
@@ -266,10 +269,46 @@ static __device__ void block_last_accepted(const DevJob& j, int* s_tmp) {
   }
   int run = (t > 0) ? s_tmp[t - 1] : -1;  // exclusive prefix
   for (int i = lo; i < hi; ++i) {
-    j.work[i] = run;
+    out[i] = run;
     if (j.k[i] > 0) run = i;
   }
   __syncthreads();
+}
+
+// One grid-wide resolution pass, part 2: search again, for the chains that
+// the marking pass queued in work[0..pending), with their corrected input.
+template <class Factory, bool TSMEM>
+__global__ void __launch_bounds__(128) research_kernel(const DevJob j, const int cpw, const uint64_t t0,
+                                                       const int64_t S, const uint32_t r) {
+  const int pending = static_cast<int>(j.stats[kStatPending]);
+  const int first = blockIdx.x * (blockDim.x >> 5) * cpw;
+  if (first >= pending) return;  // uniform per block
+  const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, false);
+  BlockCtx b = block_setup<TSMEM>(j, sp, cpw, first, false);
+  __syncthreads();
+  if (!b.active || b.chain >= pending) return;
+  const int i = j.work[b.chain];
+  if (j.xused[i] < 0) {
+    j.k[i] = 1;
+    return;
+  }
+  SearchHook<false> hk;
+  hk.tj = j.tj + static_cast<size_t>(i) * j.np1;
+  hk.D = nullptr;
+  hk.k = 0;
+  hk.M = S * j.N;
+  hk.found = 0;
+  hk.chain = static_cast<uint32_t>(i);
+  hk.r = r;
+  hk.k0 = j.key0;
+  hk.k1 = j.key1;
+  hk.jr = make_uint4(0u, 0u, 0u, 0u);
+  hk.cur_level = -1;
+  hk.run = 0u;
+  hk.done = false;
+  replay_chain<Factory>(j, b, i, t0, S, hk);
+  j.k[i] = hk.found;
+  atomicAdd(reinterpret_cast<unsigned long long*>(&j.stats[kStatSearched]), static_cast<unsigned long long>(hk.k));
 }
 
 // Resolution of the speculation, one block: the actual input of chain i is
@@ -289,7 +328,7 @@ __global__ void __launch_bounds__(128) resolve_kernel(const DevJob j, const int 
   long long searched = 0;
   int passes = 0, mism_total = 0;
   for (;;) {
-    block_last_accepted(j, s_tmp);
+    block_last_accepted(j, s_tmp, j.work);
     if (threadIdx.x == 0) s_count = 0;
     __syncthreads();
     // list of chains whose input changed (j.work reused: first the scan
@@ -362,8 +401,8 @@ __global__ void __launch_bounds__(128) resolve_kernel(const DevJob j, const int 
       j.stats[kStatCarry] = j.m[last];
       j.stats[kStatCarryValid] = 1;
     }
-    j.stats[kStatMismatch] = mism_total;
-    j.stats[kStatPasses] = passes;
+    j.stats[kStatMismatch] += mism_total;
+    j.stats[kStatPasses] += passes;
   }
   if (searched) atomicAdd(reinterpret_cast<unsigned long long*>(&j.stats[kStatSearched]),
                           static_cast<unsigned long long>(searched));
@@ -449,6 +488,15 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
       cudaSuccess)
     return e;
   ks<<<grid, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r);
+  auto kq = research_kernel<F, TS>;
+  if ((e = cudaFuncSetAttribute(kq, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=
+      cudaSuccess)
+    return e;
+  for (int pass = 0; pass < kGridPasses; ++pass) {
+    if ((e = join_mark(j, st)) != cudaSuccess) return e;
+    kq<<<grid, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r);
+    launches_add(1);
+  }
   auto kr = resolve_kernel<F, TS>;
   if ((e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=
       cudaSuccess)

@@ -38,6 +38,7 @@ struct DevJob {
   uint32_t* tj;        // [p][np1] joint thresholds for each chain's input
   int64_t* offsets;    // [p] position of each kept segment in the joined chain
   int32_t* work;       // [p] scratch list of chains
+  int32_t* lastacc;    // [p] last chain before i that kept samples (-1: none)
   int32_t* trace;      // [S][p] energy after each sweep (nullable)
   long long* stats;    // [kStatCount] small device counters
 };
@@ -46,12 +47,13 @@ enum StatIndex : int {
   kStatCarry = 0,        // level passed on to the next round's chain 0
   kStatCarryValid = 1,
   kStatJoined = 2,       // samples kept in the last joint
-  kStatMismatch = 3,     // chains whose speculated input was wrong (last joint)
-  kStatPasses = 4,       // resolve passes of the last joint
+  kStatMismatch = 3,     // searches repeated because the speculated input was wrong
+  kStatPasses = 4,       // resolution passes that had work (last joint)
   kStatRejected = 5,     // chains with no kept sample (last joint)
   kStatSearched = 6,     // samples replayed by the last joint's searches
   kStatJoinedTotal = 7,  // samples kept by all joints of the job
-  kStatCount = 8
+  kStatPending = 8,      // chains queued for the current resolution pass
+  kStatCount = 12
 };
 
 // ---- kernels (mc_kernels.cu) ----
@@ -65,7 +67,9 @@ cudaError_t k_join(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S
                    bool naive, cudaStream_t st);
 
 // pieces of the joint shared by all lattice sizes
+constexpr int kGridPasses = 6;  // grid-wide resolution passes before the one-block fallback
 cudaError_t join_prelude(const DevJob& j, cudaStream_t st);
+cudaError_t join_mark(const DevJob& j, cudaStream_t st);
 cudaError_t join_finalize(const DevJob& j, int64_t S, cudaStream_t st);
 
 // per-unit launchers of the templated chain kernels (mc_inst_*.cu)

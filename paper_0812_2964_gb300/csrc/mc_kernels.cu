@@ -173,7 +173,53 @@ __global__ void naive_kernel(const DevJob j) {
 }
 
 __global__ void clear_stats_kernel(const DevJob j) {
-  if (threadIdx.x == 0) j.stats[kStatSearched] = 0;
+  if (threadIdx.x == 0) {
+    j.stats[kStatSearched] = 0;
+    j.stats[kStatMismatch] = 0;
+    j.stats[kStatPasses] = 0;
+    j.stats[kStatPending] = 0;
+  }
+}
+
+// One grid-wide resolution pass, part 1 (one block): with the current k's,
+// the actual input of chain i is the last level of the nearest chain before
+// it that kept samples (or the carry).  Chains whose k was computed for
+// another input are queued in work[], with the new input in xused, and
+// their joint thresholds are rebuilt by tj_list_kernel.
+__global__ void __launch_bounds__(1024) mark_kernel(const DevJob j) {
+  __shared__ int s_tmp[1024];
+  __shared__ int s_count;
+  block_last_accepted(j, s_tmp, j.lastacc);
+  if (threadIdx.x == 0) s_count = 0;
+  __syncthreads();
+  const int carry_in = j.stats[kStatCarryValid] ? static_cast<int>(j.stats[kStatCarry]) : -1;
+  for (int i = threadIdx.x; i < j.p; i += blockDim.x) {
+    const int last = j.lastacc[i];
+    const int x = (last >= 0) ? j.m[last] : carry_in;
+    if (x != j.xused[i]) {
+      j.xused[i] = x;
+      j.k[i] = -1;
+      j.work[atomicAdd(&s_count, 1)] = i;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    j.stats[kStatPending] = s_count;
+    if (s_count) {
+      j.stats[kStatPasses] += 1;
+      j.stats[kStatMismatch] += s_count;
+    }
+  }
+}
+
+__global__ void tj_list_kernel(const DevJob j) {
+  const long long total = j.stats[kStatPending] * static_cast<long long>(j.np1);
+  for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int i = j.work[idx / j.np1], m = static_cast<int>(idx % j.np1);
+    const int x = j.xused[i];
+    j.tj[static_cast<size_t>(i) * j.np1 + m] = (x < 0) ? 0xFFFFFFFFu : threshold_det(__dsub_rn(j.W[m], j.W[x]));
+  }
 }
 
 // ------------------------------------------------------------------ host side
@@ -207,6 +253,13 @@ cudaError_t join_prelude(const DevJob& j, cudaStream_t st) {
   clear_stats_kernel<<<1, 32, 0, st>>>(j);
   tj_kernel<<<blocks_for(static_cast<long long>(j.p) * j.np1, 256), 256, 0, st>>>(j, nullptr, j.p);
   launches_add(3);
+  return cudaGetLastError();
+}
+
+cudaError_t join_mark(const DevJob& j, cudaStream_t st) {
+  mark_kernel<<<1, 1024, 0, st>>>(j);
+  tj_list_kernel<<<256, 256, 0, st>>>(j);
+  launches_add(2);
   return cudaGetLastError();
 }
 

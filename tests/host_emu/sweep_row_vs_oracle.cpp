@@ -1,0 +1,77 @@
+// CPU check of the GPU row sweep (mc_chain.cuh, compiled for the host):
+// every chain is swept with sweep_row and with the oracle's or_chain_round
+// from the same start; lattices, levels, per-sweep levels and dwell-time
+// histograms must agree exactly, and the level index must stay in [0, N].
+
+#include "mc_chain.cuh"
+extern "C" {
+#include "mc_oracle.h"
+}
+using namespace mcgpu;
+
+template <int WD>
+int run(int L, int p, int64_t S, uint64_t seed, const double* W, int start) {
+  const int N = L * L, np1 = N + 1;
+  std::vector<uint32_t> Tor(5 * np1), T(5 * np1);
+  or_build_table(W, L, Tor.data());
+  for (int m = 0; m < np1; ++m) for (int a = 0; a < 5; ++a) T[a * np1 + m] = Tor[m * 5 + a];
+  int bad = 0;
+  for (int c = 0; c < p; ++c) {
+    std::vector<int8_t> s(N);
+    or_init_lattice(s.data(), L, seed, c, start);
+    int m_or = (or_energy(s.data(), L) + 2 * N) / 4;
+    // pack
+    std::vector<uint32_t> lat(L * WD, 0);
+    for (int y = 0; y < L; ++y) for (int x = 0; x < L; ++x) if (s[y * L + x] > 0) lat[y * WD + x / 32] |= 1u << (x % 32);
+    int m = m_or;
+    std::vector<uint32_t> hist(np1, 0);
+    GenHook hk{hist.data(), 0};
+    Prefetch pf; prefetch_init<WD>(pf, L, 0, (uint32_t)c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    std::vector<int32_t> tr_g(S);
+    for (int64_t sw = 0; sw < S; ++sw) {
+      for (int y = 0; y < L; ++y) {
+        int ym = (y + L - 1) % L, yp = (y + 1) % L;
+        uint32_t cur[WD], up[WD], dn[WD];
+        for (int w = 0; w < WD; ++w) { cur[w] = lat[y * WD + w]; up[w] = lat[ym * WD + w]; dn[w] = lat[yp * WD + w]; }
+        sweep_row<WD>(cur, up, dn, L, m, T.data(), np1, pf, (uint32_t)c, (uint32_t)seed, (uint32_t)(seed >> 32), hk);
+        if (m < 0 || m > N) { printf("m out of range %d\n", m); return 1; }
+        for (int w = 0; w < WD; ++w) lat[y * WD + w] = cur[w];
+      }
+      tr_g[sw] = m;
+    }
+    hk.flush(m);
+    // oracle
+    std::vector<int32_t> tr(S); std::vector<int64_t> h(np1, 0);
+    int32_t mo = m_or;
+    or_chain_round(L, seed, c, 0, S, Tor.data(), s.data(), &mo, tr.data(), h.data(), nullptr);
+    std::vector<uint32_t> lat2(L * WD, 0);
+    for (int y = 0; y < L; ++y) for (int x = 0; x < L; ++x) if (s[y * L + x] > 0) lat2[y * WD + x / 32] |= 1u << (x % 32);
+    bool ok = (lat == lat2) && (mo == m);
+    for (int64_t sw = 0; sw < S; ++sw) ok = ok && tr[sw] == tr_g[sw];
+    for (int q = 0; q < np1; ++q) ok = ok && (int64_t)hist[q] == h[q];
+    if (!ok) { ++bad; if (bad < 3) printf("L=%d chain %d mismatch (m %d vs %d)\n", L, c, m, mo); }
+  }
+  return bad;
+}
+int main() {
+  int total_bad = 0;
+  int Ls[] = {4, 8, 12, 16, 20, 24, 28, 32, 36, 48, 64, 100, 128};
+  for (int L : Ls) {
+    int N = L * L;
+    std::vector<double> W(N + 1);
+    srand(L);
+    for (int i = 0; i <= N; ++i) W[i] = 3.0 * ((double)rand() / RAND_MAX - 0.5) + 2.0 * sin(i * 0.01);
+    int64_t S = L <= 32 ? 20 : 4;
+    int p = L <= 32 ? 8 : 3;
+    int wd = (L + 31) / 32, bad = 0;
+    for (int start = 0; start < 2; ++start) {
+      if (wd == 1) bad += run<1>(L, p, S, 0x1234567890ull + L, W.data(), start);
+      else if (wd == 2) bad += run<2>(L, p, S, 0x1234567890ull + L, W.data(), start);
+      else if (wd == 3) bad += run<3>(L, p, S, 0x1234567890ull + L, W.data(), start);
+      else bad += run<4>(L, p, S, 0x1234567890ull + L, W.data(), start);
+    }
+    printf("L=%d: %s\n", L, bad ? "MISMATCH" : "ok");
+    total_bad += bad;
+  }
+  return total_bad != 0;
+}
