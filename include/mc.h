@@ -157,6 +157,32 @@ int mc_set_launch_shape(mc_job *job, int placement, int chains_per_warp, int war
 /* Wait for the job's queued work. */
 int mc_sync(mc_job *job);
 
+/* One round of chain generation (what mc_run_sweeps does for a job) on
+ * caller-owned DEVICE buffers, without allocating any device memory.  The
+ * paper has no counterpart: this exists for callers that cannot allocate
+ * while they run (a host function inside a stream, a process whose device
+ * memory is fully reserved up front, a pool that forbids foreign
+ * allocations).
+ *   d_spins   [n_chains][L][ceil(L/32)] uint32, read and overwritten;
+ *   d_levels  [n_chains] int32, level m = (E + 2N)/4 of each lattice, updated;
+ *   d_weights [N+1] double, W = ln w (read);
+ *   d_hist    [N+1] int64, zeroed, then the number of this round's samples
+ *             at each level;
+ *   t0        attempts each chain made before this round (multiple of 4),
+ *             so that round r of a job started at t0 = 0 uses t0 = r*M.
+ * Work is queued on cuda_stream (NULL = legacy default stream); returns
+ * without waiting.  Scratch: the threshold table lives in one fixed
+ * 320 KiB device array (L <= 128) that the library holds on every device
+ * until the process exits; L > 128 is rejected with MC_EINVAL.  The first
+ * call on a device looks up that array's address (cudaGetSymbolAddress)
+ * and must therefore come before any stream capture on that device.  All
+ * calls share the array and it keeps the last call's contents: calls that
+ * overlap on the GPU (other streams, other threads) race on it and must be
+ * serialised by the caller. */
+int mc_generate_noalloc(int L, int n_chains, uint64_t seed, uint64_t t0, int64_t n_sweeps,
+                        uint32_t *d_spins, int32_t *d_levels, const double *d_weights,
+                        int64_t *d_hist, void *cuda_stream);
+
 /* Number of kernels this library has launched since it was loaded. */
 uint64_t mc_kernel_launches(void);
 

@@ -19,7 +19,8 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_init", "mc_free", "mc_set_stream", "mc_set_trace", "mc_run_sweeps", "mc_join",
     "mc_join_naive", "mc_histogram", "mc_update_weights", "mc_get_weights", "mc_set_weights",
     "mc_get_table", "mc_get_spins", "mc_set_spins", "mc_get_energies", "mc_get_trace",
-    "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error"]
+    "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error",
+    "mc_generate_noalloc"]
 
 # revision of the generation kernel; bump when it changes (profiles record it)
 KERNEL_REV = "gen-2"
@@ -86,6 +87,9 @@ def lib():
             "mc_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(mc_info)]),
             "mc_set_launch_shape": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
             "mc_sync": (ctypes.c_int, [_vp]),
+            "mc_generate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                                   ctypes.c_uint64, ctypes.c_int64, _vp, _vp, _vp,
+                                                   _vp, _vp]),
             "mc_kernel_launches": (ctypes.c_uint64, []),
             "mc_last_error": (ctypes.c_char_p, []),
         }
@@ -208,6 +212,13 @@ def mc_set_launch_shape(job, placement: int, chains_per_warp: int, warps_per_blo
 
 def mc_sync(job):
     _check(lib().mc_sync(job))
+
+
+def mc_generate_noalloc(L: int, n_chains: int, seed: int, t0: int, n_sweeps: int, d_spins: int,
+                        d_levels: int, d_weights: int, d_hist: int, stream: int | None = None):
+    """Device pointers (ints) in, nothing allocated; see include/mc.h."""
+    _check(lib().mc_generate_noalloc(L, n_chains, seed, t0, n_sweeps, _vp(d_spins), _vp(d_levels),
+                                     _vp(d_weights), _vp(d_hist), _vp(stream or 0)))
 
 
 def mc_last_error() -> str:

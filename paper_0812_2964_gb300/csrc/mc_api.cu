@@ -14,8 +14,12 @@ using mcgpu::DevJob;
 using mcgpu::LaunchShape;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+void mcgpu::set_last_error(const char* msg) { g_err = msg; }
+
+namespace {
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];

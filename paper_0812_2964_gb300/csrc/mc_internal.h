@@ -90,6 +90,9 @@ LaunchShape default_shape(int L, int p, int num_sms);
 bool shape_supported(int L, const LaunchShape& s);
 size_t gen_smem_bytes(int L, const LaunchShape& s, bool* table_in_smem);
 
+// message returned by mc_last_error() on this thread
+void set_last_error(const char* msg);
+
 // total kernel launches issued by this library (for accounting)
 uint64_t launches_add(uint64_t n);
 
