@@ -40,7 +40,7 @@ WORKLOAD = "L32_p16384"
 # Integer operations one single-spin-flip attempt needs (derivation in
 # the design doc): Philox4x32-10 amortised over its 4 words (10), aligned-
 # neighbour count (7), threshold index + load (2), compare (1), flip + level
-# update (2), dwell-time histogram (3).
+# update (2), histogram update (3).
 ALG_OPS_PER_ATTEMPT = 25
 SMS, SUBPARTITIONS, LANES = 152, 4, 32
 L2_FLUSH_BYTES = 256 << 20
@@ -297,8 +297,8 @@ def run_gpu(args):
     gen_attempts = p * M
     achieved = gen_attempts * ALG_OPS_PER_ATTEMPT / gen_s
     tr = _traffic_record()
-    traffic = tr.get("bytes_per_launch") if tr.get("workload") == WORKLOAD and \
-        tr.get("sweeps") == S and tr.get("kernel_rev") == mc.KERNEL_REV else None
+    traffic = tr.get("bytes_per_launch") if (tr.get("workload") == WORKLOAD and tr.get("sweeps") == S
+                                             and tr.get("kernel_rev") == mc.KERNEL_REV) else None
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
