@@ -154,6 +154,17 @@ int mc_get_info(mc_job *job, mc_info *info);
  * dynamics and all results are independent of this choice. */
 int mc_set_launch_shape(mc_job *job, int placement, int chains_per_warp, int warps_per_block);
 
+/* Pick the launch shape by measurement: every supported combination of
+ * placement, chains per warp and warps per block is timed on a scratch copy
+ * of the job's chains (probe_sweeps sweeps each, CUDA events on the job's
+ * stream; the job's own chains do not move) and the fastest is kept for the
+ * job.  With use_cache != 0 a shape found earlier for the same device, L and
+ * n_chains is reused without timing.  The chosen shape is returned through
+ * the (nullable) out pointers.  The paper has no counterpart (launch tuning).
+ * Allocates and frees temporary device memory; synchronises. */
+int mc_autotune(mc_job *job, int64_t probe_sweeps, int use_cache, int *placement,
+                int *chains_per_warp, int *warps_per_block);
+
 /* Wait for the job's queued work. */
 int mc_sync(mc_job *job);
 

@@ -20,7 +20,7 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_join_naive", "mc_histogram", "mc_update_weights", "mc_get_weights", "mc_set_weights",
     "mc_get_table", "mc_get_spins", "mc_set_spins", "mc_get_energies", "mc_get_trace",
     "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error",
-    "mc_generate_noalloc"]
+    "mc_generate_noalloc", "mc_autotune"]
 
 # revision of the generation kernel; bump when it changes (profiles record it)
 KERNEL_REV = "gen-2"
@@ -87,6 +87,9 @@ def lib():
             "mc_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(mc_info)]),
             "mc_set_launch_shape": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
             "mc_sync": (ctypes.c_int, [_vp]),
+            "mc_autotune": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]),
             "mc_generate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                                    ctypes.c_uint64, ctypes.c_int64, _vp, _vp, _vp,
                                                    _vp, _vp]),
@@ -210,6 +213,13 @@ def mc_set_launch_shape(job, placement: int, chains_per_warp: int, warps_per_blo
     _check(lib().mc_set_launch_shape(job, placement, chains_per_warp, warps_per_block))
 
 
+def mc_autotune(job, probe_sweeps: int, use_cache: bool = True):
+    pl, c, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().mc_autotune(job, probe_sweeps, 1 if use_cache else 0, ctypes.byref(pl),
+                             ctypes.byref(c), ctypes.byref(w)))
+    return int(pl.value), int(c.value), int(w.value)
+
+
 def mc_sync(job):
     _check(lib().mc_sync(job))
 
@@ -258,6 +268,9 @@ class Job:
 
     def set_launch_shape(self, placement, cpw, wpb):
         mc_set_launch_shape(self.h, placement, cpw, wpb)
+
+    def autotune(self, probe_sweeps: int, use_cache: bool = True):
+        return mc_autotune(self.h, probe_sweeps, use_cache)
 
     def run_sweeps(self, S: int):
         mc_run_sweeps(self.h, S)

@@ -3,8 +3,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/mc.h"
@@ -379,6 +382,103 @@ int mc_get_info(mc_job* job, mc_info* info) {
   info->chains_per_warp = job->shape.cpw;
   info->warps_per_block = job->shape.wpb;
   info->device_bytes = job->bytes;
+  return MC_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Candidate launch shapes are timed on a scratch copy of the job's lattices
+// and levels (so the job's own chains are not advanced), with CUDA events on
+// the job's stream; the fastest is kept for the job and cached per
+// (device, L, n_chains) for later jobs.  Every shape gives identical results.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, LaunchShape> g_tune_cache;
+}  // namespace
+
+int mc_autotune(mc_job* job, int64_t probe_sweeps, int use_cache, int* placement, int* cpw, int* wpb) {
+  if (int rc = check_job(job)) return rc;
+  if (job->pending) return fail(MC_ESTATE, "round pending");
+  if (probe_sweeps < 1 || probe_sweeps * job->N >= (int64_t(1) << 34)) return fail(MC_EINVAL, "bad probe_sweeps");
+  const auto key = std::make_tuple(job->device, job->L, job->p);
+  if (use_cache) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      job->shape = it->second;
+      if (placement) *placement = job->shape.placement;
+      if (cpw) *cpw = job->shape.cpw;
+      if (wpb) *wpb = job->shape.wpb;
+      return MC_OK;
+    }
+  }
+  // candidate shapes
+  std::vector<LaunchShape> cands;
+  const int sub = job->num_sms * 4;
+  std::vector<int> cpws = {1, 2, 4, 8, 16, 32};
+  for (int w = 1; w <= 4; w *= 2) {
+    cpws.push_back((job->p + sub - 1) / sub);
+    cpws.push_back((job->p + job->num_sms * w - 1) / (job->num_sms * w));
+    cpws.push_back((job->p + 2 * sub - 1) / (2 * sub));
+  }
+  for (int pl = 0; pl < 2; ++pl)
+    for (int w = 1; w <= 4; w *= 2)
+      for (int c : cpws) {
+        LaunchShape s{pl, std::min(32, std::max(1, c)), w};
+        if (!mcgpu::shape_supported(job->L, s)) continue;
+        bool dup = false;
+        for (const auto& q : cands) dup = dup || (q.placement == s.placement && q.cpw == s.cpw && q.wpb == s.wpb);
+        if (!dup) cands.push_back(s);
+      }
+  // scratch copy of the chain state
+  DevJob d = job->d;
+  const size_t lat = static_cast<size_t>(job->p) * job->L * job->wd;
+  void *sp = nullptr, *sm = nullptr, *sh = nullptr;
+  cudaError_t e = cudaMalloc(&sp, lat * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&sm, static_cast<size_t>(job->p) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&sh, static_cast<size_t>(d.np1) * 8);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  LaunchShape best = job->shape;
+  float best_ms = 1e30f;
+  if (e == cudaSuccess) {
+    d.spins = static_cast<uint32_t*>(sp);
+    d.m = static_cast<int32_t*>(sm);
+    d.hgen = static_cast<unsigned long long*>(sh);
+    d.trace = nullptr;
+    for (const auto& s : cands) {
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms up
+        e = cudaMemcpyAsync(d.spins, job->d.spins, lat * 4, cudaMemcpyDeviceToDevice, job->stream);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(d.m, job->d.m, static_cast<size_t>(job->p) * 4, cudaMemcpyDeviceToDevice, job->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, job->stream);
+        if (e == cudaSuccess) e = mcgpu::k_generate(d, s, job->t, probe_sweeps, false, job->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, job->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (e != cudaSuccess) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = s;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (sp) cudaFree(sp);
+  if (sm) cudaFree(sm);
+  if (sh) cudaFree(sh);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  job->shape = best;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  if (placement) *placement = best.placement;
+  if (cpw) *cpw = best.cpw;
+  if (wpb) *wpb = best.wpb;
   return MC_OK;
 }
 

@@ -4,6 +4,7 @@
 // sizes so that the library builds in parallel.
 #pragma once
 #include <algorithm>
+#include <type_traits>
 
 #include "mc_chain.cuh"
 #include "mc_internal.h"
@@ -48,20 +49,25 @@ struct RegRunner {
   }
 };
 
-template <int WD_>
+// SL > 0 fixes L at compile time (no per-site guards); SL == 0 reads L at run time.
+template <int WD_, int SL = 0>
 struct SmemRunner {
   static constexpr int WD = WD_;
   uint32_t* lat;  // this chain's column
-  int stride, L;
+  int stride, Lrt;
+  __device__ __forceinline__ int len() const { return SL > 0 ? SL : Lrt; }
   __device__ __forceinline__ void load(const uint32_t* __restrict__ g) {
+    const int L = len();
     for (int i = 0; i < L * WD; ++i) lat[i * stride] = g[i];
   }
   __device__ __forceinline__ void store(uint32_t* __restrict__ g) const {
+    const int L = len();
     for (int i = 0; i < L * WD; ++i) g[i] = lat[i * stride];
   }
   template <bool EARLY, class Hook>
   __device__ __forceinline__ void sweep(int& m, Prefetch& pf, const uint32_t* __restrict__ T, int np1,
                                         uint32_t chain, uint32_t k0, uint32_t k1, Hook& hk) {
+    const int L = len();
 #pragma unroll 1
     for (int y = 0; y < L; ++y) {
       const int ym = (y == 0) ? L - 1 : y - 1, yp = (y + 1 == L) ? 0 : y + 1;
@@ -135,13 +141,13 @@ template <int L>
 struct RunnerFactoryReg {
   __device__ __forceinline__ static RegRunner<L> make(const BlockCtx&, int) { return RegRunner<L>(); }
 };
-template <int WD>
+template <int WD, int SL>
 struct RunnerFactorySmem {
-  __device__ __forceinline__ static SmemRunner<WD> make(const BlockCtx& b, int L) {
-    SmemRunner<WD> r;
+  __device__ __forceinline__ static SmemRunner<WD, SL> make(const BlockCtx& b, int L) {
+    SmemRunner<WD, SL> r;
     r.lat = b.lat + b.slot;
     r.stride = b.nslot;
-    r.L = L;
+    r.Lrt = L;
     return r;
   }
 };
@@ -441,8 +447,8 @@ template <int L>
 struct RegF : RunnerFactoryReg<L> {
   static constexpr int kPlacement = kPlaceReg;
 };
-template <int WD>
-struct SmemF : RunnerFactorySmem<WD> {
+template <int WD, int SL = 0>
+struct SmemF : RunnerFactorySmem<WD, SL> {
   static constexpr int kPlacement = kPlaceSmem;
 };
 
@@ -512,12 +518,25 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
   return join_finalize(j, S, st);
 }
 
+// Whether a factory's lattice size is fixed at compile time with a
+// threshold table that can never fit in shared memory (then only the
+// global-table kernels are instantiated).
+template <class F>
+struct TableNeverFits : std::false_type {};
+template <int WD, int SL>
+struct TableNeverFits<SmemF<WD, SL>> : std::integral_constant<bool, (SL > 0 && 5ull * 4ull * (SL * SL + 1) > kMaxSmem)> {};
+
 template <class F>
 inline cudaError_t dispatch_ts(const DevJob& j, const LaunchShape& s, bool gen, uint64_t t0, int64_t S, bool trace,
                                uint32_t r, cudaStream_t st) {
-  const bool ts = table_fits(j.L, s, gen);
-  if (gen) return ts ? launch_gen_t<F, true>(j, s, t0, S, trace, st) : launch_gen_t<F, false>(j, s, t0, S, trace, st);
-  return ts ? launch_join_t<F, true>(j, s, t0, S, r, st) : launch_join_t<F, false>(j, s, t0, S, r, st);
+  if constexpr (TableNeverFits<F>::value) {
+    if (gen) return launch_gen_t<F, false>(j, s, t0, S, trace, st);
+    return launch_join_t<F, false>(j, s, t0, S, r, st);
+  } else {
+    const bool ts = table_fits(j.L, s, gen);
+    if (gen) return ts ? launch_gen_t<F, true>(j, s, t0, S, trace, st) : launch_gen_t<F, false>(j, s, t0, S, trace, st);
+    return ts ? launch_join_t<F, true>(j, s, t0, S, r, st) : launch_join_t<F, false>(j, s, t0, S, r, st);
+  }
 }
 
 }  // namespace mcgpu

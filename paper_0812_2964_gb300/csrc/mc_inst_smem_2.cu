@@ -1,4 +1,4 @@
-// Instantiation unit: lattice in shared memory, 2 word(s) per row.
+// Instantiation unit: lattice in shared memory, 2 word(s) per row, L read at run time.
 #include "mc_chain_kernels.cuh"
 
 namespace mcgpu {

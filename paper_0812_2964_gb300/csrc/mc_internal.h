@@ -83,6 +83,11 @@ MC_CHAIN_UNIT(chain_kernels_smem_1);
 MC_CHAIN_UNIT(chain_kernels_smem_2);
 MC_CHAIN_UNIT(chain_kernels_smem_3);
 MC_CHAIN_UNIT(chain_kernels_smem_4);
+MC_CHAIN_UNIT(chain_kernels_smem_L48);
+MC_CHAIN_UNIT(chain_kernels_smem_L64);
+MC_CHAIN_UNIT(chain_kernels_smem_L96);
+MC_CHAIN_UNIT(chain_kernels_smem_L100);
+MC_CHAIN_UNIT(chain_kernels_smem_L128);
 #undef MC_CHAIN_UNIT
 
 // launch shape chosen by default for (L, p)

@@ -276,6 +276,14 @@ static cudaError_t dispatch(const DevJob& j, const LaunchShape& s, bool gen, uin
     if (j.L <= 28) return chain_kernels_reg_b(j, s, gen, t0, S, trace, r, st);
     return chain_kernels_reg_c(j, s, gen, t0, S, trace, r, st);
   }
+  switch (j.L) {
+    case 48: return chain_kernels_smem_L48(j, s, gen, t0, S, trace, r, st);
+    case 64: return chain_kernels_smem_L64(j, s, gen, t0, S, trace, r, st);
+    case 96: return chain_kernels_smem_L96(j, s, gen, t0, S, trace, r, st);
+    case 100: return chain_kernels_smem_L100(j, s, gen, t0, S, trace, r, st);
+    case 128: return chain_kernels_smem_L128(j, s, gen, t0, S, trace, r, st);
+    default: break;
+  }
   switch (j.wd) {
     case 1: return chain_kernels_smem_1(j, s, gen, t0, S, trace, r, st);
     case 2: return chain_kernels_smem_2(j, s, gen, t0, S, trace, r, st);

@@ -174,3 +174,23 @@ def test_set_spins_roundtrip_and_energy():
     g.spin_words = oracle.pack_spins(s)
     assert np.array_equal(g.spin_words, oracle.pack_spins(s))
     assert list(g.energies) == [oracle.energy(s[c]) for c in range(p)]
+
+
+def test_autotune_picks_a_supported_shape_and_keeps_results():
+    L, p, S = 32, 200, 2
+    g = mc.Job(L, p, 31, 1)
+    W = random_weights(L, 5, 3.0)
+    g.weights = W
+    shape = g.autotune(probe_sweeps=2, use_cache=False)
+    assert shape[0] in (0, 1) and 1 <= shape[1] <= 32 and 1 <= shape[2] <= 4
+    info = g.info()
+    assert (info["placement"], info["chains_per_warp"], info["warps_per_block"]) == shape
+    o = oracle.Job(L, p, 31, 1)
+    o.weights = W
+    _compare_state(g, o, L)         # tuning did not move the chains
+    g.run_sweeps(S)
+    o.run_round(S, nthreads=8)
+    _compare_state(g, o, L)
+    assert g.join() == o.join()
+    assert np.array_equal(g.hist, o.hist)
+    assert mc.mc_autotune(g.h, 2, True) == shape   # cached
