@@ -154,6 +154,18 @@ int mc_get_info(mc_job *job, mc_info *info);
  * dynamics and all results are independent of this choice. */
 int mc_set_launch_shape(mc_job *job, int placement, int chains_per_warp, int warps_per_block);
 
+/* `iterations` weight iterations (round of n_sweeps sweeps, joint, weight
+ * update -- Sec. 2 and Eq. new_weight) of n_jobs independent jobs, queued on
+ * the first job's stream.  mode 0: one generation launch per job and round;
+ * mode 1: one fused generation launch per round for all jobs whose lattice
+ * size has a fused form (L = 8, 16, 24, 32 in registers; 48, 64 in shared
+ * memory; up to 8 jobs), the others keep their own launch; mode 2: mode 1
+ * with the whole loop captured once as a CUDA graph and launched.  The
+ * chains, and so every result, are the same in all modes.  Synchronises.
+ * No round may be pending on any job.  The paper has no counterpart: a
+ * scheduling form of running independent weight estimations together. */
+int mc_batch_run(mc_job **jobs, int n_jobs, int iterations, int64_t n_sweeps, int mode);
+
 /* Pick the launch shape by measurement: every supported combination of
  * placement, chains per warp and warps per block is timed on a scratch copy
  * of the job's chains (probe_sweeps sweeps each, CUDA events on the job's

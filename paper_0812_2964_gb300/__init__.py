@@ -20,7 +20,7 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_join_naive", "mc_histogram", "mc_update_weights", "mc_get_weights", "mc_set_weights",
     "mc_get_table", "mc_get_spins", "mc_set_spins", "mc_get_energies", "mc_get_trace",
     "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error",
-    "mc_generate_noalloc", "mc_autotune"]
+    "mc_generate_noalloc", "mc_autotune", "mc_batch_run"]
 
 # revision of the generation kernel; bump when it changes (profiles record it)
 KERNEL_REV = "gen-2"
@@ -87,6 +87,8 @@ def lib():
             "mc_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(mc_info)]),
             "mc_set_launch_shape": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
             "mc_sync": (ctypes.c_int, [_vp]),
+            "mc_batch_run": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int64, ctypes.c_int]),
             "mc_autotune": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int)]),
@@ -218,6 +220,13 @@ def mc_autotune(job, probe_sweeps: int, use_cache: bool = True):
     _check(lib().mc_autotune(job, probe_sweeps, 1 if use_cache else 0, ctypes.byref(pl),
                              ctypes.byref(c), ctypes.byref(w)))
     return int(pl.value), int(c.value), int(w.value)
+
+
+def mc_batch_run(jobs, iterations: int, n_sweeps: int, mode: int):
+    """jobs: list of handles (or Job objects)."""
+    hs = [j.h if isinstance(j, Job) else j for j in jobs]
+    arr = (_vp * len(hs))(*[h.value if isinstance(h, _vp) else h for h in hs])
+    _check(lib().mc_batch_run(arr, len(hs), iterations, n_sweeps, mode))
 
 
 def mc_sync(job):

@@ -1,5 +1,6 @@
 // C ABI (include/mc.h): job lifetime, device memory, stream ordering and
 // argument checking around the kernels of mc_kernels.cu.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -11,6 +12,7 @@
 #include <vector>
 
 #include "../../include/mc.h"
+#include "mc_batch.h"
 #include "mc_internal.h"
 
 using mcgpu::DevJob;
@@ -82,6 +84,12 @@ int dalloc(mc_job* j, T** p, size_t count) {
 void free_all(mc_job* j) {
   for (void* v : j->allocs) cudaFree(v);
   j->allocs.clear();
+  if (j->d.ckpt) cudaFree(j->d.ckpt);
+  if (j->d.ckm) cudaFree(j->d.ckm);
+  if (j->d.first) cudaFree(j->d.first);
+  j->d.ckpt = nullptr;
+  j->d.ckm = nullptr;
+  j->d.first = nullptr;
   if (j->d.trace) cudaFree(j->d.trace);
   j->d.trace = nullptr;
   if (j->own_stream) cudaStreamDestroy(j->own_stream);
@@ -145,7 +153,7 @@ int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
   if ((rc = dalloc(j, &d.spins, lat)) || (rc = dalloc(j, &d.spins0, lat)) || (rc = dalloc(j, &d.m, n_chains)) ||
       (rc = dalloc(j, &d.m0, n_chains)) || (rc = dalloc(j, &d.W, np1)) || (rc = dalloc(j, &d.T, 5 * np1)) ||
       (rc = dalloc(j, &d.h, np1)) || (rc = dalloc(j, &d.hgen, np1)) || (rc = dalloc(j, &d.dpre, np1)) ||
-      (rc = dalloc(j, &d.k, n_chains)) || (rc = dalloc(j, &d.kspec, n_chains)) ||
+      (rc = dalloc(j, &d.k, n_chains)) ||
       (rc = dalloc(j, &d.xused, n_chains)) || (rc = dalloc(j, &d.tj, static_cast<size_t>(n_chains) * np1)) ||
       (rc = dalloc(j, &d.offsets, n_chains)) || (rc = dalloc(j, &d.work, n_chains)) ||
       (rc = dalloc(j, &d.lastacc, n_chains)) ||
@@ -207,41 +215,115 @@ int mc_set_launch_shape(mc_job* job, int placement, int cpw, int wpb) {
   return MC_OK;
 }
 
-int mc_run_sweeps(mc_job* job, int64_t n_sweeps) {
-  if (int rc = check_job(job)) return rc;
+}  // extern "C"
+
+namespace {
+
+// Segments of a round for the joint's parallel replays: at least 32 (or S),
+// and short enough that a block's 32-bit per-level counters cannot overflow
+// (at most 2^25 samples per segment).
+void round_segments(const mc_job* job, int64_t n_sweeps, int* K, int* C) {
+  const int64_t M = n_sweeps * job->N;
+  int64_t k = std::max<int64_t>(32, (M + (int64_t(1) << 25) - 1) >> 25);
+  k = std::min<int64_t>(k, n_sweeps);
+  const int64_t c = (n_sweeps + k - 1) / k;
+  *C = static_cast<int>(c);
+  *K = static_cast<int>((n_sweeps + c - 1) / c);
+}
+
+// Checkpoint buffers for at least K segments.
+int ensure_segments(mc_job* job, int K) {
+  DevJob& d = job->d;
+  if (K <= d.kcap && d.ckpt) return MC_OK;
+  const size_t lw = static_cast<size_t>(job->L) * job->wd;
+  const size_t p = static_cast<size_t>(job->p);
+  if (d.ckpt) {
+    cudaStreamSynchronize(job->stream);
+    cudaFree(d.ckpt);
+    cudaFree(d.ckm);
+    cudaFree(d.first);
+    job->bytes -= static_cast<size_t>(d.kcap) * p * (lw * 4 + 4 + 8);
+    d.ckpt = nullptr;
+    d.ckm = nullptr;
+    d.first = nullptr;
+    d.kcap = 0;
+  }
+  void *a = nullptr, *b = nullptr, *c = nullptr;
+  cudaError_t e = cudaMalloc(&a, static_cast<size_t>(K) * lw * p * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&b, static_cast<size_t>(K) * p * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&c, static_cast<size_t>(K) * p * 8);
+  if (e != cudaSuccess) {
+    if (a) cudaFree(a);
+    if (b) cudaFree(b);
+    if (c) cudaFree(c);
+    return cuda_fail(e, "checkpoint allocation");
+  }
+  d.ckpt = static_cast<uint32_t*>(a);
+  d.ckm = static_cast<int32_t*>(b);
+  d.first = static_cast<int64_t*>(c);
+  d.kcap = K;
+  job->bytes += static_cast<size_t>(K) * p * (lw * 4 + 4 + 8);
+  return MC_OK;
+}
+
+// Device trace buffer big enough for n_sweeps sweeps of every chain.
+int ensure_trace(mc_job* job, int64_t n_sweeps) {
+  DevJob& d = job->d;
+  const size_t need = static_cast<size_t>(n_sweeps) * job->p;
+  if (need <= job->trace_cap) return MC_OK;
+  if (d.trace) {
+    cudaStreamSynchronize(job->stream);
+    cudaFree(d.trace);
+    job->bytes -= job->trace_cap * sizeof(int32_t);
+    d.trace = nullptr;
+    job->trace_cap = 0;
+  }
+  void* v = nullptr;
+  MC_CUDA(cudaMalloc(&v, need * sizeof(int32_t)), "trace allocation");
+  d.trace = static_cast<int32_t*>(v);
+  job->trace_cap = need;
+  job->bytes += need * sizeof(int32_t);
+  return MC_OK;
+}
+
+// Start a round: checks, round-start copies (for the joint's replays) and the
+// host bookkeeping; *t0 = attempts each chain made before this round.
+int round_prepare(mc_job* job, int64_t n_sweeps, uint64_t* t0) {
   if (job->pending) return fail(MC_ESTATE, "previous round not joined");
   if (n_sweeps < 1) return fail(MC_EINVAL, "n_sweeps=%lld", static_cast<long long>(n_sweeps));
   const int64_t M = n_sweeps * job->N;
   if (n_sweeps > (int64_t(1) << 34) / job->N || M >= (int64_t(1) << 34))
     return fail(MC_EINVAL, "n_sweeps * N must stay below 2^34");
+  if (job->trace_on)
+    if (int rc = ensure_trace(job, n_sweeps)) return rc;
+  int K = 0, C = 0;
+  round_segments(job, n_sweeps, &K, &C);
+  if (int rc = ensure_segments(job, K)) return rc;
   DevJob& d = job->d;
-  if (job->trace_on) {
-    const size_t need = static_cast<size_t>(n_sweeps) * job->p;
-    if (need > job->trace_cap) {
-      if (d.trace) {
-        cudaStreamSynchronize(job->stream);
-        cudaFree(d.trace);
-        job->bytes -= job->trace_cap * sizeof(int32_t);
-        d.trace = nullptr;
-        job->trace_cap = 0;
-      }
-      void* v = nullptr;
-      MC_CUDA(cudaMalloc(&v, need * sizeof(int32_t)), "trace allocation");
-      d.trace = static_cast<int32_t*>(v);
-      job->trace_cap = need;
-      job->bytes += need * sizeof(int32_t);
-    }
-  }
+  d.ck_K = K;
+  d.ck_C = C;
   const size_t lat = static_cast<size_t>(job->p) * job->L * job->wd;
   MC_CUDA(cudaMemcpyAsync(d.spins0, d.spins, lat * sizeof(uint32_t), cudaMemcpyDeviceToDevice, job->stream),
           "round-start copy");
   MC_CUDA(cudaMemcpyAsync(d.m0, d.m, job->p * sizeof(int32_t), cudaMemcpyDeviceToDevice, job->stream),
           "round-start copy");
-  MC_CUDA(mcgpu::k_generate(d, job->shape, job->t, n_sweeps, job->trace_on, job->stream), "generation");
+  *t0 = job->t;
   job->t += static_cast<uint64_t>(M);
   job->last_S = n_sweeps;
   job->pending = true;
   job->trace_valid = job->trace_on;
+  return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mc_run_sweeps(mc_job* job, int64_t n_sweeps) {
+  if (int rc = check_job(job)) return rc;
+  uint64_t t0 = 0;
+  if (int rc = round_prepare(job, n_sweeps, &t0)) return rc;
+  MC_CUDA(mcgpu::k_generate(job->d, job->shape, t0, n_sweeps, job->trace_on, job->stream), "generation");
   return MC_OK;
 }
 
@@ -279,6 +361,121 @@ int mc_update_weights(mc_job* job) {
   if (int rc = check_job(job)) return rc;
   if (job->pending) return fail(MC_ESTATE, "round pending: join first");
   MC_CUDA(mcgpu::k_update_weights(job->d, job->stream), "weight update");
+  return MC_OK;
+}
+
+// ------------------------------------------------------------------ batches
+// `iterations` weight iterations of several independent jobs, everything on
+// the first job's stream: per iteration every job runs one round of n_sweeps
+// sweeps, is joined and updates its weight.  mode 0: one generation launch
+// per job; 1: one fused generation launch for all jobs that fit it (others
+// keep their own launch); 2: as 1, with the whole loop captured once as a
+// CUDA graph and launched.  Results are identical in all modes.
+int mc_batch_run(mc_job** jobs, int n_jobs, int iterations, int64_t n_sweeps, int mode) {
+  if (!jobs || n_jobs < 1) return fail(MC_EINVAL, "no jobs");
+  if (mode < 0 || mode > 2) return fail(MC_EINVAL, "mode=%d: 0 per-job, 1 fused, 2 fused + graph", mode);
+  if (iterations < 1) return fail(MC_EINVAL, "iterations=%d", iterations);
+  if (mode > 0 && n_jobs > mcgpu::kMaxBatch) return fail(MC_EINVAL, "at most %d jobs per fused batch", mcgpu::kMaxBatch);
+  for (int i = 0; i < n_jobs; ++i) {
+    if (!jobs[i]) return fail(MC_EINVAL, "job %d is null", i);
+    if (jobs[i]->pending) return fail(MC_ESTATE, "job %d has a round pending", i);
+    if (jobs[i]->device != jobs[0]->device) return fail(MC_EINVAL, "jobs on different devices");
+    for (int k = 0; k < i; ++k)
+      if (jobs[k] == jobs[i]) return fail(MC_EINVAL, "job %d listed twice", i);
+  }
+  cudaStream_t st = jobs[0]->stream;
+  std::vector<cudaStream_t> saved(n_jobs);
+  for (int i = 0; i < n_jobs; ++i) {
+    MC_CUDA(cudaStreamSynchronize(jobs[i]->stream), "batch start");
+    saved[i] = jobs[i]->stream;
+    jobs[i]->stream = st;
+  }
+  // shapes for the fused launch: the job's own shape when it fits, else the
+  // block shape of the fused launch with the job's chains per warp
+  std::vector<LaunchShape> bshape(n_jobs);
+  std::vector<char> fused(n_jobs, 0);
+  for (int i = 0; i < n_jobs && mode > 0; ++i) {
+    LaunchShape s = jobs[i]->shape;
+    if (!mcgpu::batch_supported(jobs[i]->L, s)) {
+      s.placement = jobs[i]->L <= 32 ? mcgpu::kPlaceReg : mcgpu::kPlaceSmem;
+      s.wpb = mcgpu::kBatchWarps;
+      while (s.cpw > 1 && !mcgpu::batch_supported(jobs[i]->L, s)) s.cpw >>= 1;
+    }
+    bshape[i] = s;
+    fused[i] = mcgpu::batch_supported(jobs[i]->L, s) ? 1 : 0;
+  }
+  int rc = MC_OK;
+  for (int i = 0; i < n_jobs && rc == MC_OK; ++i) {  // no allocation inside a capture
+    if (jobs[i]->trace_on) rc = ensure_trace(jobs[i], n_sweeps);
+    int K = 0, C = 0;
+    round_segments(jobs[i], n_sweeps, &K, &C);
+    if (rc == MC_OK) rc = ensure_segments(jobs[i], K);
+  }
+  bool capturing = false;
+  if (rc == MC_OK && mode == 2) {
+    const cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) rc = cuda_fail(e, "graph capture");
+    else capturing = true;
+  }
+  for (int it = 0; it < iterations && rc == MC_OK; ++it) {
+    mcgpu::BatchParams P;
+    P.n = 0;
+    size_t smem = 0;
+    int blocks = 0;
+    for (int i = 0; i < n_jobs && rc == MC_OK; ++i) {
+      uint64_t t0 = 0;
+      if ((rc = round_prepare(jobs[i], n_sweeps, &t0))) break;
+      cudaError_t e = cudaSuccess;
+      if (mode > 0 && fused[i]) {
+        mcgpu::BatchItem& item = P.items[P.n++];
+        size_t b = 0;
+        int nb = 0;
+        mcgpu::batch_item(jobs[i]->d, bshape[i], t0, n_sweeps, jobs[i]->trace_on, &item, &b, &nb);
+        item.first_block = blocks;
+        blocks += nb;
+        smem = std::max(smem, b);
+      } else {
+        e = mcgpu::k_generate(jobs[i]->d, jobs[i]->shape, t0, n_sweeps, jobs[i]->trace_on, st);
+      }
+      if (e != cudaSuccess) rc = cuda_fail(e, "generation");
+    }
+    if (rc == MC_OK && P.n > 0) {
+      const cudaError_t e = mcgpu::k_generate_batched(P, smem, blocks, st);
+      if (e != cudaSuccess) rc = cuda_fail(e, "batched generation");
+    }
+    for (int i = 0; i < n_jobs && rc == MC_OK; ++i) {
+      mc_job* j = jobs[i];
+      const int64_t M = j->last_S * j->N;
+      cudaError_t e = mcgpu::k_join(j->d, j->shape, j->t - static_cast<uint64_t>(M), j->last_S, j->r, false, st);
+      if (e == cudaSuccess) e = mcgpu::k_update_weights(j->d, st);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(e, "joint / weight update");
+        break;
+      }
+      j->r += 1;
+      j->pending = false;
+    }
+  }
+  if (capturing) {
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc == MC_OK && e != cudaSuccess) rc = cuda_fail(e, "graph capture");
+    if (rc == MC_OK) {
+      cudaGraphExec_t ge = nullptr;
+      cudaError_t e2 = cudaGraphInstantiate(&ge, g, 0);
+      if (e2 == cudaSuccess) e2 = cudaGraphLaunch(ge, st);
+      if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+      if (ge) cudaGraphExecDestroy(ge);
+      if (e2 != cudaSuccess) rc = cuda_fail(e2, "graph launch");
+    }
+    if (g) cudaGraphDestroy(g);
+  }
+  for (int i = 0; i < n_jobs; ++i) jobs[i]->stream = saved[i];
+  if (rc != MC_OK) {
+    for (int i = 0; i < n_jobs; ++i) jobs[i]->pending = false;
+    return rc;
+  }
+  MC_CUDA(cudaStreamSynchronize(st), "batch");
   return MC_OK;
 }
 
@@ -446,6 +643,7 @@ int mc_autotune(mc_job* job, int64_t probe_sweeps, int use_cache, int* placement
     d.m = static_cast<int32_t*>(sm);
     d.hgen = static_cast<unsigned long long*>(sh);
     d.trace = nullptr;
+    d.ckpt = nullptr;  // probes write no checkpoints
     for (const auto& s : cands) {
       float ms = 0.f;
       for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms up

@@ -30,6 +30,15 @@ struct RegRunner {
 #pragma unroll
     for (int y = 0; y < L; ++y) g[y] = R[y];
   }
+  // word y of this chain at g[y * stride] (checkpoint layout [word][chain])
+  __device__ __forceinline__ void save_strided(uint32_t* __restrict__ g, size_t stride) const {
+#pragma unroll
+    for (int y = 0; y < L; ++y) g[y * stride] = R[y];
+  }
+  __device__ __forceinline__ void load_strided(const uint32_t* __restrict__ g, size_t stride) {
+#pragma unroll
+    for (int y = 0; y < L; ++y) R[y] = g[y * stride];
+  }
   template <bool EARLY, class Hook>
   __device__ __forceinline__ void sweep(int& m, Prefetch& pf, const uint32_t* __restrict__ T, int np1,
                                         uint32_t chain, uint32_t k0, uint32_t k1, Hook& hk) {
@@ -63,6 +72,14 @@ struct SmemRunner {
   __device__ __forceinline__ void store(uint32_t* __restrict__ g) const {
     const int L = len();
     for (int i = 0; i < L * WD; ++i) g[i] = lat[i * stride];
+  }
+  __device__ __forceinline__ void save_strided(uint32_t* __restrict__ g, size_t gstride) const {
+    const int L = len();
+    for (int i = 0; i < L * WD; ++i) g[i * gstride] = lat[i * stride];
+  }
+  __device__ __forceinline__ void load_strided(const uint32_t* __restrict__ g, size_t gstride) {
+    const int L = len();
+    for (int i = 0; i < L * WD; ++i) lat[i * stride] = g[i * gstride];
   }
   template <bool EARLY, class Hook>
   __device__ __forceinline__ void sweep(int& m, Prefetch& pf, const uint32_t* __restrict__ T, int np1,
@@ -155,11 +172,13 @@ struct RunnerFactorySmem {
 // Step 2: every chain performs S sweeps (M = S N attempts) under the current
 // weight; per-level dwell counts accumulate in shared memory, then in the
 // round histogram hgen.  trace[s][c] = energy after sweep s.
+// (The body is a device function so that the batched launch can run it for
+// one of several jobs per block.)
 template <class Factory, bool TSMEM>
-__global__ void __launch_bounds__(128) gen_kernel(const DevJob j, const int cpw, const uint64_t t0,
-                                                  const int64_t S, const int64_t flushF, const int do_trace) {
+__device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const uint64_t t0, const int64_t S,
+                                         const int64_t flushF, const int do_trace, const int block) {
   const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, true);
-  const int first = blockIdx.x * (blockDim.x >> 5) * cpw;
+  const int first = block * (blockDim.x >> 5) * cpw;
   BlockCtx b = block_setup<TSMEM>(j, sp, cpw, first, true);
   auto run = Factory::make(b, j.L);
   __syncthreads();
@@ -171,8 +190,15 @@ __global__ void __launch_bounds__(128) gen_kernel(const DevJob j, const int cpw,
     m = j.m[b.chain];
     prefetch_init<decltype(run)::WD>(pf, j.L, t0, static_cast<uint32_t>(b.chain), j.key0, j.key1);
   }
+  const size_t lw = static_cast<size_t>(j.L) * j.wd;
   for (int64_t s = 0; s < S; ++s) {
     if (b.active) {
+      if (j.ckpt && (s % j.ck_C) == 0) {
+        // lattice and level at the start of segment s / C, for the joint's replays
+        const size_t seg = static_cast<size_t>(s / j.ck_C);
+        run.save_strided(j.ckpt + seg * lw * j.p + b.chain, static_cast<size_t>(j.p));
+        j.ckm[seg * j.p + b.chain] = m;
+      }
       run.template sweep<false>(m, pf, b.T, j.np1, static_cast<uint32_t>(b.chain), j.key0, j.key1, hk);
       if (do_trace) j.trace[s * j.p + b.chain] = 4 * m - 2 * j.N;
     }
@@ -203,6 +229,12 @@ __global__ void __launch_bounds__(128) gen_kernel(const DevJob j, const int cpw,
   }
 }
 
+template <class Factory, bool TSMEM>
+__global__ void __launch_bounds__(128) gen_kernel(const DevJob j, const int cpw, const uint64_t t0,
+                                                  const int64_t S, const int64_t flushF, const int do_trace) {
+  gen_body<Factory, TSMEM>(j, cpw, t0, S, flushF, do_trace, blockIdx.x);
+}
+
 // ------------------------------------------------------------------ joint: replays
 // Replay chain i from its round-start configuration with the round's flip
 // counters and run a hook over its samples.
@@ -218,27 +250,55 @@ __device__ __forceinline__ void replay_chain(const DevJob& j, const BlockCtx& b,
     run.template sweep<true>(m, pf, b.T, j.np1, static_cast<uint32_t>(i), j.key0, j.key1, hk);
 }
 
-// Speculative joint search (step 4 with input = last level of chain i-1):
-// k of the first accepted sample, and the discarded prefix added to dpre.
+// Replay one segment of chain i's round (sweeps [seg*C, min(seg*C + C, S)))
+// from its checkpoint, with the round's flip counters, running hook hk on
+// its samples (sample indices continue from the segment's start).
+template <class Factory, class Hook>
+__device__ __forceinline__ void replay_segment(const DevJob& j, const BlockCtx& b, int i, int seg, uint64_t t0,
+                                               int64_t S, Hook& hk) {
+  auto run = Factory::make(b, j.L);
+  const size_t lw = static_cast<size_t>(j.L) * j.wd;
+  run.load_strided(j.ckpt + static_cast<size_t>(seg) * lw * j.p + i, static_cast<size_t>(j.p));
+  int m = j.ckm[static_cast<size_t>(seg) * j.p + i];
+  const int64_t s0 = static_cast<int64_t>(seg) * j.ck_C;
+  const int64_t s1 = min(S, s0 + j.ck_C);
+  Prefetch pf;
+  prefetch_init<decltype(run)::WD>(pf, j.L, t0 + static_cast<uint64_t>(s0) * j.N, static_cast<uint32_t>(i), j.key0,
+                                   j.key1);
+  for (int64_t s = s0; s < s1 && !hk.done; ++s)
+    run.template sweep<true>(m, pf, b.T, j.np1, static_cast<uint32_t>(i), j.key0, j.key1, hk);
+}
+
+// Joint search (step 4) on all segments at once: work item (chain, segment),
+// one thread each, finds the first sample inside the segment that passes the
+// Metropolis test against the chain's input level, or 0.  Work items are
+// segment-major so that a warp reads one checkpoint word of consecutive
+// chains.  Listed chains only (the resolution passes) when use_list is set.
 template <class Factory, bool TSMEM>
-__global__ void __launch_bounds__(128) spec_kernel(const DevJob j, const int cpw, const uint64_t t0,
-                                                   const int64_t S, const uint32_t r) {
+__global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int cpw, const uint64_t t0,
+                                                     const int64_t S, const uint32_t r, const int use_list) {
+  const int nchains = use_list ? static_cast<int>(j.stats[kStatPending]) : j.p;
+  const long long items = static_cast<long long>(nchains) * j.ck_K;
+  const long long first_item = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) * cpw;
+  if (first_item >= items) return;  // uniform per block
   const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, false);
-  const int first = blockIdx.x * (blockDim.x >> 5) * cpw;
-  BlockCtx b = block_setup<TSMEM>(j, sp, cpw, first, false);
+  BlockCtx b = block_setup<TSMEM>(j, sp, cpw, 0, false);
   __syncthreads();
-  if (!b.active) return;
-  const int i = b.chain;
+  const long long item = first_item + b.slot;
+  if (b.lane >= cpw || item >= items) return;
+  const int seg = static_cast<int>(item / nchains);
+  const int q = static_cast<int>(item % nchains);
+  const int i = use_list ? j.work[q] : q;
   const int x = j.xused[i];
-  int64_t k;
+  int64_t found;
   if (x < 0) {
-    k = 1;  // job's first joint: chain 0 is kept whole
+    found = (seg == 0) ? 1 : 0;  // job's first joint: chain 0 is kept whole
   } else {
-    SearchHook<true> hk;
+    SearchHook<false> hk;
     hk.tj = j.tj + static_cast<size_t>(i) * j.np1;
-    hk.D = j.dpre;
-    hk.k = 0;
-    hk.M = S * j.N;
+    hk.D = nullptr;
+    hk.k = static_cast<int64_t>(seg) * j.ck_C * j.N;
+    hk.M = min(S, static_cast<int64_t>(seg + 1) * j.ck_C) * j.N;
     hk.found = 0;
     hk.chain = static_cast<uint32_t>(i);
     hk.r = r;
@@ -248,11 +308,63 @@ __global__ void __launch_bounds__(128) spec_kernel(const DevJob j, const int cpw
     hk.cur_level = -1;
     hk.run = 0u;
     hk.done = false;
-    replay_chain<Factory>(j, b, i, t0, S, hk);
-    k = hk.found;
+    const int64_t k_begin = hk.k;
+    replay_segment<Factory>(j, b, i, seg, t0, S, hk);
+    found = hk.found;
+    atomicAdd(reinterpret_cast<unsigned long long*>(&j.stats[kStatSearched]),
+              static_cast<unsigned long long>(hk.k - k_begin));
   }
-  j.k[i] = k;
-  j.kspec[i] = k;
+  j.first[static_cast<size_t>(i) * j.kcap + seg] = found;
+}
+
+// Discarded prefixes (samples 1 .. k_i - 1, the whole round when nothing is
+// kept) added to dpre, segment by segment in parallel: every sample adds 1
+// to its level in the block's shared histogram, flushed at the end.  A
+// segment holds at most 2^32 / 128 samples, so the 32-bit counters of a
+// block cannot overflow.
+struct PrefixHook {
+  uint32_t* hist;
+  int64_t k, cut;  // samples with index < cut are counted
+  bool done;
+  __device__ __forceinline__ void sample(int m4) {
+    if (done) return;
+    ++k;
+    if (k >= cut) {
+      done = true;
+      return;
+    }
+    red_shared_add(hist, m4, 1u);
+  }
+};
+
+template <class Factory, bool TSMEM>
+__global__ void __launch_bounds__(128) prefix_kernel(const DevJob j, const int cpw, const uint64_t t0,
+                                                     const int64_t S) {
+  const long long items = static_cast<long long>(j.p) * j.ck_K;
+  const long long first_item = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) * cpw;
+  if (first_item >= items) return;  // uniform per block
+  const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, true);
+  BlockCtx b = block_setup<TSMEM>(j, sp, cpw, 0, true);
+  __syncthreads();
+  const long long item = first_item + b.slot;
+  if (b.lane < cpw && item < items) {
+    const int seg = static_cast<int>(item / j.p);
+    const int i = static_cast<int>(item % j.p);
+    const int64_t M = S * j.N;
+    const int64_t k = j.k[i];
+    const int64_t cut = (k > 0) ? k : M + 1;
+    const int64_t seg_first = static_cast<int64_t>(seg) * j.ck_C * j.N + 1;
+    if (seg_first < cut) {
+      PrefixHook hk{b.hist, seg_first - 1, cut, false};
+      replay_segment<Factory>(j, b, i, seg, t0, S, hk);
+    }
+  }
+  asm volatile("" ::: "memory");
+  __syncthreads();
+  for (int m = threadIdx.x; m < j.np1; m += blockDim.x) {
+    const uint32_t v = b.hist[m];
+    if (v) atomicAdd(&j.dpre[m], static_cast<unsigned long long>(v));
+  }
 }
 
 // Block-wide scan: out[i] = index of the last chain before i whose k > 0
@@ -279,42 +391,6 @@ __device__ __forceinline__ void block_last_accepted(const DevJob& j, int* s_tmp,
     if (j.k[i] > 0) run = i;
   }
   __syncthreads();
-}
-
-// One grid-wide resolution pass, part 2: search again, for the chains that
-// the marking pass queued in work[0..pending), with their corrected input.
-template <class Factory, bool TSMEM>
-__global__ void __launch_bounds__(128) research_kernel(const DevJob j, const int cpw, const uint64_t t0,
-                                                       const int64_t S, const uint32_t r) {
-  const int pending = static_cast<int>(j.stats[kStatPending]);
-  const int first = blockIdx.x * (blockDim.x >> 5) * cpw;
-  if (first >= pending) return;  // uniform per block
-  const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, false);
-  BlockCtx b = block_setup<TSMEM>(j, sp, cpw, first, false);
-  __syncthreads();
-  if (!b.active || b.chain >= pending) return;
-  const int i = j.work[b.chain];
-  if (j.xused[i] < 0) {
-    j.k[i] = 1;
-    return;
-  }
-  SearchHook<false> hk;
-  hk.tj = j.tj + static_cast<size_t>(i) * j.np1;
-  hk.D = nullptr;
-  hk.k = 0;
-  hk.M = S * j.N;
-  hk.found = 0;
-  hk.chain = static_cast<uint32_t>(i);
-  hk.r = r;
-  hk.k0 = j.key0;
-  hk.k1 = j.key1;
-  hk.jr = make_uint4(0u, 0u, 0u, 0u);
-  hk.cur_level = -1;
-  hk.run = 0u;
-  hk.done = false;
-  replay_chain<Factory>(j, b, i, t0, S, hk);
-  j.k[i] = hk.found;
-  atomicAdd(reinterpret_cast<unsigned long long*>(&j.stats[kStatSearched]), static_cast<unsigned long long>(hk.k));
 }
 
 // Resolution of the speculation, one block: the actual input of chain i is
@@ -414,34 +490,6 @@ __global__ void __launch_bounds__(128) resolve_kernel(const DevJob j, const int 
                           static_cast<unsigned long long>(searched));
 }
 
-// Chains whose final k differs from the speculated one: move the samples
-// between the two prefix ends into or out of the discarded histogram.
-template <class Factory, bool TSMEM>
-__global__ void __launch_bounds__(128) correct_kernel(const DevJob j, const int cpw, const uint64_t t0,
-                                                      const int64_t S) {
-  const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, false);
-  const int first = blockIdx.x * (blockDim.x >> 5) * cpw;
-  BlockCtx b = block_setup<TSMEM>(j, sp, cpw, first, false);
-  __syncthreads();
-  if (!b.active) return;
-  const int i = b.chain;
-  const int64_t M = S * j.N;
-  const int64_t ks = j.kspec[i], kf = j.k[i];
-  if (ks == kf) return;
-  const int64_t es = ks > 0 ? ks : M + 1, ef = kf > 0 ? kf : M + 1;
-  CorrectHook hk;
-  hk.D = j.dpre;
-  hk.k = 0;
-  hk.lo = min(es, ef);
-  hk.hi = max(es, ef);
-  hk.sign = (ef > es) ? 1ull : ~0ull;  // +1 or -1
-  hk.cur_level = -1;
-  hk.run = 0u;
-  hk.done = false;
-  replay_chain<Factory>(j, b, i, t0, S, hk);
-  hk.flush();
-}
-
 // ------------------------------------------------------------------ host-side launchers
 template <int L>
 struct RegF : RunnerFactoryReg<L> {
@@ -485,35 +533,36 @@ template <class F, bool TS>
 inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S, uint32_t r,
                                  cudaStream_t st) {
   const size_t bytes = plan_bytes(j.L, s, TS, false);
+  const size_t pbytes = plan_bytes(j.L, s, TS, true);
   const int per_block = s.cpw * s.wpb;
-  const unsigned grid = blocks_for(j.p, per_block);
+  const unsigned grid_all = blocks_for(static_cast<long long>(j.p) * j.ck_K, per_block);
   cudaError_t e = join_prelude(j, st);
   if (e != cudaSuccess) return e;
-  auto ks = spec_kernel<F, TS>;
-  if ((e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=
-      cudaSuccess)
-    return e;
-  ks<<<grid, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r);
-  auto kq = research_kernel<F, TS>;
+  auto kq = search_kernel<F, TS>;
   if ((e = cudaFuncSetAttribute(kq, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=
       cudaSuccess)
     return e;
+  // speculated inputs: every chain, every segment
+  kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, 0);
+  if ((e = join_select(j, false, st)) != cudaSuccess) return e;
+  // grid-wide resolution passes (the listed chains' items fit in grid_all)
   for (int pass = 0; pass < kGridPasses; ++pass) {
     if ((e = join_mark(j, st)) != cudaSuccess) return e;
-    kq<<<grid, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r);
-    launches_add(1);
+    kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, 1);
+    if ((e = join_select(j, true, st)) != cudaSuccess) return e;
   }
+  launches_add(1 + kGridPasses);
   auto kr = resolve_kernel<F, TS>;
   if ((e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=
       cudaSuccess)
     return e;
   kr<<<1, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r);
-  auto kc = correct_kernel<F, TS>;
-  if ((e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=
+  auto kp = prefix_kernel<F, TS>;
+  if ((e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(pbytes))) !=
       cudaSuccess)
     return e;
-  kc<<<grid, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S);
-  launches_add(3);
+  kp<<<grid_all, 32 * s.wpb, pbytes, st>>>(j, s.cpw, t0, S);
+  launches_add(2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return join_finalize(j, S, st);
 }
@@ -533,7 +582,8 @@ inline cudaError_t dispatch_ts(const DevJob& j, const LaunchShape& s, bool gen, 
     if (gen) return launch_gen_t<F, false>(j, s, t0, S, trace, st);
     return launch_join_t<F, false>(j, s, t0, S, r, st);
   } else {
-    const bool ts = table_fits(j.L, s, gen);
+    // the joint's prefix pass needs the histogram beside the table, like generation
+    const bool ts = table_fits(j.L, s, true);
     if (gen) return ts ? launch_gen_t<F, true>(j, s, t0, S, trace, st) : launch_gen_t<F, false>(j, s, t0, S, trace, st);
     return ts ? launch_join_t<F, true>(j, s, t0, S, r, st) : launch_join_t<F, false>(j, s, t0, S, r, st);
   }

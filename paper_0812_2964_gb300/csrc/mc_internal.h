@@ -33,13 +33,18 @@ struct DevJob {
   unsigned long long* hgen;  // [np1] all samples of the round
   unsigned long long* dpre;  // [np1] discarded prefixes of the round
   int64_t* k;          // [p] first kept sample (0 = none) after the joint
-  int64_t* kspec;      // [p] first kept sample under the speculated input
   int32_t* xused;      // [p] input level the current k was computed for (-1 = none)
   uint32_t* tj;        // [p][np1] joint thresholds for each chain's input
   int64_t* offsets;    // [p] position of each kept segment in the joined chain
   int32_t* work;       // [p] scratch list of chains
   int32_t* lastacc;    // [p] last chain before i that kept samples (-1: none)
   int32_t* trace;      // [S][p] energy after each sweep (nullable)
+  uint32_t* ckpt;      // [kcap][L*wd][p] lattice at the start of each round segment
+  int32_t* ckm;        // [kcap][p] level at the start of each round segment
+  int64_t* first;      // [p][kcap] first accepted sample inside each segment (0: none)
+  int ck_C;            // sweeps per segment in the current round
+  int ck_K;            // segments in the current round
+  int kcap;            // segment capacity
   long long* stats;    // [kStatCount] small device counters
 };
 
@@ -70,6 +75,7 @@ cudaError_t k_join(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S
 constexpr int kGridPasses = 6;  // grid-wide resolution passes before the one-block fallback
 cudaError_t join_prelude(const DevJob& j, cudaStream_t st);
 cudaError_t join_mark(const DevJob& j, cudaStream_t st);
+cudaError_t join_select(const DevJob& j, bool listed, cudaStream_t st);
 cudaError_t join_finalize(const DevJob& j, int64_t S, cudaStream_t st);
 
 // per-unit launchers of the templated chain kernels (mc_inst_*.cu)

@@ -161,7 +161,6 @@ __global__ void naive_kernel(const DevJob j) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < j.p) {
     j.k[i] = 1;
-    j.kspec[i] = 1;
     j.xused[i] = -1;
   }
   if (i == 0) {
@@ -253,6 +252,28 @@ cudaError_t join_prelude(const DevJob& j, cudaStream_t st) {
   clear_stats_kernel<<<1, 32, 0, st>>>(j);
   tj_kernel<<<blocks_for(static_cast<long long>(j.p) * j.np1, 256), 256, 0, st>>>(j, nullptr, j.p);
   launches_add(3);
+  return cudaGetLastError();
+}
+
+// k_i = the first accepted sample of the first segment that has one (0: none).
+__global__ void select_kernel(const DevJob j, const int listed) {
+  const int n = listed ? static_cast<int>(j.stats[kStatPending]) : j.p;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int i = listed ? j.work[q] : q;
+  const int64_t* f = j.first + static_cast<size_t>(i) * j.kcap;
+  int64_t k = 0;
+  for (int s = 0; s < j.ck_K; ++s)
+    if (f[s] > 0) {
+      k = f[s];
+      break;
+    }
+  j.k[i] = k;
+}
+
+cudaError_t join_select(const DevJob& j, bool listed, cudaStream_t st) {
+  select_kernel<<<blocks_for(j.p, 256), 256, 0, st>>>(j, listed ? 1 : 0);
+  launches_add(1);
   return cudaGetLastError();
 }
 
