@@ -205,7 +205,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     mc.build()
-    w = WORKLOADS[WORKLOAD]
+    w = WORKLOADS[args.workload]
     S = args.sweeps or w.sweeps
     p, N = w.chains, w.N
     M = S * N
@@ -213,6 +213,8 @@ def run_gpu(args):
     job = mc.Job(w.L, p, w.seed + rank, w.start)
     job.set_stream(stream.cuda_stream)
     job.set_trace(True)
+    if args.tune:
+        job.autotune(probe_sweeps=max(1, min(S, 4_000_000 // N)))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
 
     with torch.cuda.stream(stream):
@@ -297,7 +299,7 @@ def run_gpu(args):
     gen_attempts = p * M
     achieved = gen_attempts * ALG_OPS_PER_ATTEMPT / gen_s
     tr = _traffic_record()
-    traffic = tr.get("bytes_per_launch") if (tr.get("workload") == WORKLOAD and tr.get("sweeps") == S
+    traffic = tr.get("bytes_per_launch") if (tr.get("workload") == args.workload and tr.get("sweeps") == S
                                              and tr.get("kernel_rev") == mc.KERNEL_REV) else None
 
     cpu = None
@@ -308,7 +310,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "L": w.L, "chains": p, "sweeps_per_iteration": S,
+        "config": {"workload": args.workload, "L": w.L, "chains": p, "sweeps_per_iteration": S,
                    "start": "random" if w.start else "all up", "seed": w.seed,
                    "weight_iterations_timed": f"{args.warmup + 1}..{args.warmup + args.steps}",
                    "l2": "flushed between steps (256 MB write)", "trace": "int32 per sweep",
@@ -320,7 +322,7 @@ def run_gpu(args):
         "raw_attempts_per_s": args.steps * p * M * world / t_max,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
                      "unit": "Gop/s", "frac": achieved / peak_ops, "traffic": traffic,
-                     "kernel": "gen_kernel (lattice rows in registers)",
+                     "kernel": "gen_kernel (lattice rows in %s)" % ["registers", "shared memory"][info["placement"]],
                      "kernel_ms": statistics.mean(gen_ms),
                      "ops_per_attempt": ALG_OPS_PER_ATTEMPT,
                      "peak_source": f"{SMS} SMs x {SUBPARTITIONS} sub-partitions x {LANES} lanes x "
@@ -340,19 +342,80 @@ def run_gpu(args):
     return 0
 
 
+def run_batch(args):
+    """The uneven batch: L in {16, 24, 32, 48, 64} with 8192/4096/4096/2048/1024
+    chains, every weight iteration run three ways -- one generation launch per
+    job, one fused launch, the fused loop as a CUDA graph -- on the same
+    chains (identical results); value = the graph form's kept samples/s."""
+    import torch
+
+    import paper_0812_2964_gb300 as mc
+    from paper_0812_2964_gb300.workloads import BATCH_GROUPS
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    mc.build()
+    S = args.sweeps or 50_000
+    modes = {0: "one launch per job", 1: "one fused launch", 2: "fused launch, CUDA graph"}
+    out = {}
+    for mode in (0, 1, 2):
+        jobs = [mc.Job(L, p, seed + rank, 1) for (L, p, seed) in BATCH_GROUPS]
+        for j in jobs:
+            j.set_trace(True)
+            if args.tune:
+                j.autotune(probe_sweeps=max(1, min(S, 2_000_000 // j.N)))
+        mc.mc_batch_run(jobs, args.warmup, S, mode)
+        torch.cuda.synchronize()
+        kept0 = sum(j.info()["total_joined"] for j in jobs)
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        l0 = mc.mc_kernel_launches()
+        t0 = time.perf_counter()
+        mc.mc_batch_run(jobs, args.steps, S, mode)   # synchronises
+        el = time.perf_counter() - t0
+        launches = mc.mc_kernel_launches() - l0
+        clk = clocks.stop()
+        kept = sum(j.info()["total_joined"] for j in jobs) - kept0
+        attempts = sum(j.p * S * j.N for j in jobs) * args.steps
+        out[mode] = {"mode": modes[mode], "value": kept / el, "seconds": el, "kept": kept,
+                     "raw_attempts_per_s": attempts / el, "gpu_launches": launches, "clocks": clk,
+                     "shapes": [[j.info()[k] for k in ("placement", "chains_per_warp", "warps_per_block")]
+                                for j in jobs]}
+        for j in jobs:
+            j.close()
+    best = out[2]
+    line = {"metric": METRIC, "value": best["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * best["seconds"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "batch_uneven", "groups": [list(g) for g in BATCH_GROUPS],
+                       "sweeps_per_iteration": S, "timing": "host wall clock around the synchronising call",
+                       "autotuned": bool(args.tune)},
+            "modes": out, "fused_vs_per_job": out[1]["value"] / out[0]["value"],
+            "graph_vs_per_job": out[2]["value"] / out[0]["value"], "clocks": best["clocks"],
+            "gpu_launches": best["gpu_launches"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="L32_p16384 (default), L64_p4096, L128_p1024, L8_p64, or batch_uneven")
     ap.add_argument("--sweeps", type=int, default=0, help="override sweeps per iteration")
+    ap.add_argument("--tune", action="store_true", help="pick the launch shape with mc_autotune first")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch_uneven":
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -141,6 +141,12 @@ int mc_get_energies(mc_job *job, int32_t *out, int n);
  * n >= last_sweeps * n_chains; MC_ESTATE if the trace was off.  Syncs. */
 int mc_get_trace(mc_job *job, int32_t *out, size_t n);
 
+/* Energy after each sweep of the last round for one chain: out[s] for
+ * s < last_sweeps (n >= last_sweeps).  A strided device-to-host copy of
+ * the same buffer mc_get_trace reads; MC_EINVAL for a chain out of range,
+ * MC_ESTATE if the trace was off.  Synchronises. */
+int mc_get_trace_chain(mc_job *job, int chain, int32_t *out, size_t n);
+
 /* Result of the last joint: k[i] = first kept sample of chain i (1..M) or 0
  * if none was kept; offsets[i] = position of chain i's kept segment in the
  * joined chain of that round.  Either pointer may be NULL.  Synchronises. */

@@ -19,6 +19,7 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_init", "mc_free", "mc_set_stream", "mc_set_trace", "mc_run_sweeps", "mc_join",
     "mc_join_naive", "mc_histogram", "mc_update_weights", "mc_get_weights", "mc_set_weights",
     "mc_get_table", "mc_get_spins", "mc_set_spins", "mc_get_energies", "mc_get_trace",
+    "mc_get_trace_chain",
     "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error",
     "mc_generate_noalloc", "mc_autotune", "mc_batch_run"]
 
@@ -83,6 +84,7 @@ def lib():
             "mc_set_spins": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
             "mc_get_energies": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
             "mc_get_trace": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+            "mc_get_trace_chain": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_size_t]),
             "mc_get_join": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
             "mc_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(mc_info)]),
             "mc_set_launch_shape": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -197,6 +199,12 @@ def mc_get_energies(job, out: np.ndarray):
 def mc_get_trace(job, out: np.ndarray):
     assert out.dtype == np.int32 and out.flags.c_contiguous
     _check(lib().mc_get_trace(job, _ptr(out), out.size))
+    return out
+
+
+def mc_get_trace_chain(job, chain: int, out: np.ndarray):
+    assert out.dtype == np.int32 and out.flags.c_contiguous
+    _check(lib().mc_get_trace_chain(job, int(chain), _ptr(out), out.size))
     return out
 
 
@@ -338,6 +346,10 @@ class Job:
     def trace(self):
         S = self.info()["last_sweeps"]
         return mc_get_trace(self.h, np.zeros(S * self.p, np.int32)).reshape(S, self.p)
+
+    def trace_chain(self, chain: int):
+        S = self.info()["last_sweeps"]
+        return mc_get_trace_chain(self.h, chain, np.zeros(S, np.int32))
 
     @property
     def k(self):

@@ -87,6 +87,8 @@ void free_all(mc_job* j) {
   if (j->d.ckpt) cudaFree(j->d.ckpt);
   if (j->d.ckm) cudaFree(j->d.ckm);
   if (j->d.first) cudaFree(j->d.first);
+  if (j->d.plist) cudaFree(j->d.plist);
+  j->d.plist = nullptr;
   j->d.ckpt = nullptr;
   j->d.ckm = nullptr;
   j->d.first = nullptr;
@@ -220,11 +222,10 @@ int mc_set_launch_shape(mc_job* job, int placement, int cpw, int wpb) {
 namespace {
 
 // Segments of a round for the joint's parallel replays: at least 32 (or S),
-// and short enough that a block's 32-bit per-level counters cannot overflow
-// (at most 2^25 samples per segment).
+// and at most 2^24 samples each (the prefix pass relies on that bound).
 void round_segments(const mc_job* job, int64_t n_sweeps, int* K, int* C) {
   const int64_t M = n_sweeps * job->N;
-  int64_t k = std::max<int64_t>(32, (M + (int64_t(1) << 25) - 1) >> 25);
+  int64_t k = std::max<int64_t>(32, (M + (int64_t(1) << 24) - 1) >> 24);
   k = std::min<int64_t>(k, n_sweeps);
   const int64_t c = (n_sweeps + k - 1) / k;
   *C = static_cast<int>(c);
@@ -242,27 +243,32 @@ int ensure_segments(mc_job* job, int K) {
     cudaFree(d.ckpt);
     cudaFree(d.ckm);
     cudaFree(d.first);
-    job->bytes -= static_cast<size_t>(d.kcap) * p * (lw * 4 + 4 + 8);
+    cudaFree(d.plist);
+    job->bytes -= static_cast<size_t>(d.kcap) * p * (lw * 4 + 4 + 8 + 8);
     d.ckpt = nullptr;
     d.ckm = nullptr;
     d.first = nullptr;
+    d.plist = nullptr;
     d.kcap = 0;
   }
-  void *a = nullptr, *b = nullptr, *c = nullptr;
+  void *a = nullptr, *b = nullptr, *c = nullptr, *w = nullptr;
   cudaError_t e = cudaMalloc(&a, static_cast<size_t>(K) * lw * p * 4);
   if (e == cudaSuccess) e = cudaMalloc(&b, static_cast<size_t>(K) * p * 4);
   if (e == cudaSuccess) e = cudaMalloc(&c, static_cast<size_t>(K) * p * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&w, static_cast<size_t>(K) * p * 8);
   if (e != cudaSuccess) {
     if (a) cudaFree(a);
     if (b) cudaFree(b);
     if (c) cudaFree(c);
+    if (w) cudaFree(w);
     return cuda_fail(e, "checkpoint allocation");
   }
   d.ckpt = static_cast<uint32_t*>(a);
   d.ckm = static_cast<int32_t*>(b);
   d.first = static_cast<int64_t*>(c);
+  d.plist = static_cast<int2*>(w);
   d.kcap = K;
-  job->bytes += static_cast<size_t>(K) * p * (lw * 4 + 4 + 8);
+  job->bytes += static_cast<size_t>(K) * p * (lw * 4 + 4 + 8 + 8);
   return MC_OK;
 }
 
@@ -539,6 +545,17 @@ int mc_get_trace(mc_job* job, int32_t* out, size_t n) {
   const size_t need = static_cast<size_t>(job->last_S) * job->p;
   if (!out || n < need) return fail(MC_EINVAL, "trace needs %zu entries", need);
   MC_CUDA(cudaMemcpyAsync(out, job->d.trace, need * 4, cudaMemcpyDeviceToHost, job->stream), "trace copy");
+  return sync(job, "trace");
+}
+
+int mc_get_trace_chain(mc_job* job, int chain, int32_t* out, size_t n) {
+  if (int rc = check_job(job)) return rc;
+  if (!job->trace_valid || !job->d.trace) return fail(MC_ESTATE, "no trace recorded for the last round");
+  if (chain < 0 || chain >= job->p) return fail(MC_EINVAL, "chain %d out of range", chain);
+  const size_t S = static_cast<size_t>(job->last_S);
+  if (!out || n < S) return fail(MC_EINVAL, "trace of one chain needs %zu entries", S);
+  MC_CUDA(cudaMemcpy2DAsync(out, 4, job->d.trace + chain, 4ull * job->p, 4, S, cudaMemcpyDeviceToHost, job->stream),
+          "trace column copy");
   return sync(job, "trace");
 }
 

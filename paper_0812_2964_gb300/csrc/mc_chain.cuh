@@ -223,83 +223,26 @@ struct GenHook {
 // Joint search (Sec. 2 step 4): for samples k = 1..M of the chain (the
 // configuration after attempt k of the round) draw the joint uniform
 // Philox((k-1)>>2, r, chain, 1) word (k-1)&3 and test it against the
-// threshold of the move from the input level x to the sample's level.  The
-// first k that passes is recorded; samples before it are the discarded
-// prefix.  If ACCUM, the prefix's levels are added (dwell-time, 64-bit
-// atomics) to a global histogram.
-template <bool ACCUM>
+// threshold of the move from the input level x to the sample's level; the
+// first k that passes is recorded.  The test does not steer control flow
+// (the threshold load would then stall every sample): hits are folded into
+// `found` branch-free and the replay loop looks at `done` once per row.
 struct SearchHook {
   const uint32_t* __restrict__ tj;  // thresholds for moves x -> m, indexed by m
-  unsigned long long* D;
   int64_t k, M, found;
   uint32_t chain, r, k0, k1;
   uint4 jr;
-  int cur_level;
-  uint32_t run;
   bool done;
   __device__ __forceinline__ void sample(int m4) {
-    if (done) return;
     const int m = m4 >> 2;
     ++k;
     const uint64_t q = static_cast<uint64_t>(k - 1);
     if ((q & 3u) == 0u)
       jr = philox4x32_10(make_uint4(static_cast<uint32_t>(q >> 2), r, chain, kTagJoint), k0, k1);
     const uint32_t u = uint4_word(jr, static_cast<uint32_t>(q & 3u));
-    if (u <= tj[m]) {
-      found = k;
-      done = true;
-      if (ACCUM) flush();
-      return;
-    }
-    if (ACCUM) {
-      if (m != cur_level) {
-        flush();
-        cur_level = m;
-      }
-      ++run;
-    }
-    if (k == M) {
-      found = 0;
-      done = true;
-      if (ACCUM) flush();
-    }
-  }
-  __device__ __forceinline__ void flush() {
-    if (run && cur_level >= 0) atomicAdd(&D[cur_level], static_cast<unsigned long long>(run));
-    run = 0u;
-  }
-};
-
-// Prefix correction: samples j in [lo, hi) (1-based) are added with the given
-// sign (+1 or -1, two's complement in the unsigned accumulator).
-struct CorrectHook {
-  unsigned long long* D;
-  int64_t k, lo, hi;
-  unsigned long long sign;
-  int cur_level;
-  uint32_t run;
-  bool done;
-  __device__ __forceinline__ void sample(int m4) {
-    if (done) return;
-    const int m = m4 >> 2;
-    ++k;
-    if (k >= hi) {
-      flush();
-      done = true;
-      return;
-    }
-    if (k >= lo) {
-      if (m != cur_level) {
-        flush();
-        cur_level = m;
-      }
-      ++run;
-    }
-  }
-  __device__ __forceinline__ void flush() {
-    if (run && cur_level >= 0)
-      atomicAdd(&D[cur_level], sign * static_cast<unsigned long long>(run));
-    run = 0u;
+    const bool hit = (u <= __ldg(&tj[m])) && !done && k <= M;
+    found = hit ? k : found;
+    done = done || hit;
   }
 };
 

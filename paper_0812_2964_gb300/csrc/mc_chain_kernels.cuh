@@ -269,59 +269,70 @@ __device__ __forceinline__ void replay_segment(const DevJob& j, const BlockCtx& 
     run.template sweep<true>(m, pf, b.T, j.np1, static_cast<uint32_t>(i), j.key0, j.key1, hk);
 }
 
-// Joint search (step 4) on all segments at once: work item (chain, segment),
-// one thread each, finds the first sample inside the segment that passes the
-// Metropolis test against the chain's input level, or 0.  Work items are
-// segment-major so that a warp reads one checkpoint word of consecutive
-// chains.  Listed chains only (the resolution passes) when use_list is set.
+// Joint search (step 4) on all segments at once: work item (chain, segment)
+// finds the first sample inside the segment that passes the Metropolis test
+// against the chain's input level (0 if none).  Persistent: each warp takes
+// the next cpw consecutive items (segment-major: one segment of consecutive
+// chains) from a global counter, its lanes replay them side by side, and
+// only then takes more, so a long replay holds up one warp, not a wave of
+// blocks.  A segment is skipped when an earlier segment of its chain has
+// already found an accepted sample (first[] is -1 until written).  Listed
+// chains only (resolution passes) when use_list is set.
 template <class Factory, bool TSMEM>
 __global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int cpw, const uint64_t t0,
                                                      const int64_t S, const uint32_t r, const int use_list) {
   const int nchains = use_list ? static_cast<int>(j.stats[kStatPending]) : j.p;
   const long long items = static_cast<long long>(nchains) * j.ck_K;
-  const long long first_item = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) * cpw;
-  if (first_item >= items) return;  // uniform per block
+  if (items == 0) return;
   const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, false);
   BlockCtx b = block_setup<TSMEM>(j, sp, cpw, 0, false);
   __syncthreads();
-  const long long item = first_item + b.slot;
-  if (b.lane >= cpw || item >= items) return;
-  const int seg = static_cast<int>(item / nchains);
-  const int q = static_cast<int>(item % nchains);
-  const int i = use_list ? j.work[q] : q;
-  const int x = j.xused[i];
-  int64_t found;
-  if (x < 0) {
-    found = (seg == 0) ? 1 : 0;  // job's first joint: chain 0 is kept whole
-  } else {
-    SearchHook<false> hk;
-    hk.tj = j.tj + static_cast<size_t>(i) * j.np1;
-    hk.D = nullptr;
-    hk.k = static_cast<int64_t>(seg) * j.ck_C * j.N;
-    hk.M = min(S, static_cast<int64_t>(seg + 1) * j.ck_C) * j.N;
-    hk.found = 0;
-    hk.chain = static_cast<uint32_t>(i);
-    hk.r = r;
-    hk.k0 = j.key0;
-    hk.k1 = j.key1;
-    hk.jr = make_uint4(0u, 0u, 0u, 0u);
-    hk.cur_level = -1;
-    hk.run = 0u;
-    hk.done = false;
-    const int64_t k_begin = hk.k;
-    replay_segment<Factory>(j, b, i, seg, t0, S, hk);
-    found = hk.found;
-    atomicAdd(reinterpret_cast<unsigned long long*>(&j.stats[kStatSearched]),
-              static_cast<unsigned long long>(hk.k - k_begin));
+  unsigned long long* queue = reinterpret_cast<unsigned long long*>(&j.stats[kStatQueueSearch]);
+  long long searched = 0;
+  for (;;) {
+    long long base = 0;
+    if (b.lane == 0) base = static_cast<long long>(atomicAdd(queue, static_cast<unsigned long long>(cpw)));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (base >= items) break;
+    const long long item = base + b.lane;
+    if (b.lane < cpw && item < items) {
+      const int seg = static_cast<int>(item / nchains);
+      const int q = static_cast<int>(item % nchains);
+      const int i = use_list ? j.work[q] : q;
+      int64_t* fi = j.first + static_cast<size_t>(i) * j.kcap;
+      bool earlier = false;
+      for (int s2 = 0; s2 < seg && !earlier; ++s2) earlier = __ldcg(&fi[s2]) > 0;
+      if (!earlier) {
+        const int x = j.xused[i];
+        int64_t found;
+        if (x < 0) {
+          found = (seg == 0) ? 1 : 0;  // job's first joint: chain 0 is kept whole
+        } else {
+          SearchHook hk;
+          hk.tj = j.tj + static_cast<size_t>(i) * j.np1;
+          hk.k = static_cast<int64_t>(seg) * j.ck_C * j.N;
+          hk.M = min(S, static_cast<int64_t>(seg + 1) * j.ck_C) * j.N;
+          hk.found = 0;
+          hk.chain = static_cast<uint32_t>(i);
+          hk.r = r;
+          hk.k0 = j.key0;
+          hk.k1 = j.key1;
+          hk.jr = make_uint4(0u, 0u, 0u, 0u);
+          hk.done = false;
+          const int64_t k_begin = hk.k;
+          replay_segment<Factory>(j, b, i, seg, t0, S, hk);
+          found = hk.found;
+          searched += hk.k - k_begin;
+        }
+        fi[seg] = found;
+      }
+    }
+    __syncwarp();
   }
-  j.first[static_cast<size_t>(i) * j.kcap + seg] = found;
+  if (searched)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&j.stats[kStatSearched]), static_cast<unsigned long long>(searched));
 }
 
-// Discarded prefixes (samples 1 .. k_i - 1, the whole round when nothing is
-// kept) added to dpre, segment by segment in parallel: every sample adds 1
-// to its level in the block's shared histogram, flushed at the end.  A
-// segment holds at most 2^32 / 128 samples, so the 32-bit counters of a
-// block cannot overflow.
 struct PrefixHook {
   uint32_t* hist;
   int64_t k, cut;  // samples with index < cut are counted
@@ -340,24 +351,48 @@ struct PrefixHook {
 template <class Factory, bool TSMEM>
 __global__ void __launch_bounds__(128) prefix_kernel(const DevJob j, const int cpw, const uint64_t t0,
                                                      const int64_t S) {
-  const long long items = static_cast<long long>(j.p) * j.ck_K;
-  const long long first_item = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) * cpw;
-  if (first_item >= items) return;  // uniform per block
+  const long long items = j.stats[kStatQueuePrefix];
+  if (items == 0) return;
   const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, true);
   BlockCtx b = block_setup<TSMEM>(j, sp, cpw, 0, true);
+  __shared__ long long s_base;
+  __shared__ unsigned long long s_samples;
+  if (threadIdx.x == 0) s_samples = 0ull;
   __syncthreads();
-  const long long item = first_item + b.slot;
-  if (b.lane < cpw && item < items) {
-    const int seg = static_cast<int>(item / j.p);
-    const int i = static_cast<int>(item % j.p);
-    const int64_t M = S * j.N;
-    const int64_t k = j.k[i];
-    const int64_t cut = (k > 0) ? k : M + 1;
-    const int64_t seg_first = static_cast<int64_t>(seg) * j.ck_C * j.N + 1;
-    if (seg_first < cut) {
+  unsigned long long* queue = reinterpret_cast<unsigned long long*>(&j.stats[kStatQueueSearch]);
+  const int slots = (blockDim.x >> 5) * cpw;
+  const int64_t M = S * j.N;
+  for (;;) {
+    if (threadIdx.x == 0) s_base = static_cast<long long>(atomicAdd(queue, static_cast<unsigned long long>(slots)));
+    __syncthreads();
+    const long long base = s_base;
+    if (base >= items) break;
+    const long long item = base + b.slot;
+    if (b.lane < cpw && item < items) {
+      const int2 w = j.plist[item];
+      const int i = w.x, seg = w.y;
+      const int64_t k = j.k[i];
+      const int64_t cut = (k > 0) ? k : M + 1;
+      const int64_t seg_first = static_cast<int64_t>(seg) * j.ck_C * j.N + 1;
       PrefixHook hk{b.hist, seg_first - 1, cut, false};
       replay_segment<Factory>(j, b, i, seg, t0, S, hk);
+      atomicAdd(&s_samples, static_cast<unsigned long long>(hk.k - (seg_first - 1)));
     }
+    asm volatile("" ::: "memory");
+    __syncthreads();
+    // a batch adds at most 128 * 2^24 = 2^31 samples: flush at 2^30
+    if (s_samples >= (1ull << 30)) {
+      for (int m = threadIdx.x; m < j.np1; m += blockDim.x) {
+        const uint32_t v = b.hist[m];
+        if (v) {
+          atomicAdd(&j.dpre[m], static_cast<unsigned long long>(v));
+          b.hist[m] = 0u;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_samples = 0ull;
+    }
+    __syncthreads();
   }
   asm volatile("" ::: "memory");
   __syncthreads();
@@ -450,9 +485,8 @@ __global__ void __launch_bounds__(128) resolve_kernel(const DevJob j, const int 
           j.k[i] = 1;
           continue;
         }
-        SearchHook<false> hk;
+        SearchHook hk;
         hk.tj = j.tj + static_cast<size_t>(i) * j.np1;
-        hk.D = nullptr;
         hk.k = 0;
         hk.M = S * j.N;
         hk.found = 0;
@@ -461,8 +495,6 @@ __global__ void __launch_bounds__(128) resolve_kernel(const DevJob j, const int 
         hk.k0 = j.key0;
         hk.k1 = j.key1;
         hk.jr = make_uint4(0u, 0u, 0u, 0u);
-        hk.cur_level = -1;
-        hk.run = 0u;
         hk.done = false;
         replay_chain<Factory>(j, b, i, t0, S, hk);
         j.k[i] = hk.found;
@@ -502,6 +534,17 @@ struct SmemF : RunnerFactorySmem<WD, SL> {
 
 constexpr size_t kMaxSmem = 227 * 1024;
 
+// Blocks of a kernel that fit on the device at once (occupancy API).
+template <class K>
+inline long long resident_blocks(K kernel, int threads, size_t smem_bytes) {
+  int dev = 0, sms = 1, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem_bytes) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return static_cast<long long>(sms) * per_sm;
+}
+
 inline bool table_fits(int L, const LaunchShape& s, bool hist) {
   const SmemPlan sp = smem_plan(L, s.placement, s.cpw, s.wpb, true, hist);
   return 4ull * (sp.table_words + sp.hist_words + sp.lat_words) <= kMaxSmem;
@@ -535,19 +578,24 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
   const size_t bytes = plan_bytes(j.L, s, TS, false);
   const size_t pbytes = plan_bytes(j.L, s, TS, true);
   const int per_block = s.cpw * s.wpb;
-  const unsigned grid_all = blocks_for(static_cast<long long>(j.p) * j.ck_K, per_block);
+  const long long items = static_cast<long long>(j.p) * j.ck_K;
   cudaError_t e = join_prelude(j, st);
   if (e != cudaSuccess) return e;
   auto kq = search_kernel<F, TS>;
   if ((e = cudaFuncSetAttribute(kq, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=
       cudaSuccess)
     return e;
+  // persistent grids: the blocks that are resident at once, no more than needed
+  const unsigned grid_all = static_cast<unsigned>(
+      std::min<long long>(blocks_for(items, per_block), resident_blocks(kq, 32 * s.wpb, bytes)));
   // speculated inputs: every chain, every segment
+  if ((e = join_reset_queue(j, st)) != cudaSuccess) return e;
   kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, 0);
   if ((e = join_select(j, false, st)) != cudaSuccess) return e;
   // grid-wide resolution passes (the listed chains' items fit in grid_all)
   for (int pass = 0; pass < kGridPasses; ++pass) {
     if ((e = join_mark(j, st)) != cudaSuccess) return e;
+    if ((e = join_reset_queue(j, st)) != cudaSuccess) return e;
     kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, 1);
     if ((e = join_select(j, true, st)) != cudaSuccess) return e;
   }
@@ -561,7 +609,11 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
   if ((e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(pbytes))) !=
       cudaSuccess)
     return e;
-  kp<<<grid_all, 32 * s.wpb, pbytes, st>>>(j, s.cpw, t0, S);
+  if ((e = join_prefix_list(j, st)) != cudaSuccess) return e;
+  if ((e = join_reset_queue(j, st)) != cudaSuccess) return e;
+  const unsigned grid_pre = static_cast<unsigned>(
+      std::min<long long>(blocks_for(items, per_block), resident_blocks(kp, 32 * s.wpb, pbytes)));
+  kp<<<grid_pre, 32 * s.wpb, pbytes, st>>>(j, s.cpw, t0, S);
   launches_add(2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return join_finalize(j, S, st);

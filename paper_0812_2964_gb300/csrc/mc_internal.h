@@ -42,6 +42,7 @@ struct DevJob {
   uint32_t* ckpt;      // [kcap][L*wd][p] lattice at the start of each round segment
   int32_t* ckm;        // [kcap][p] level at the start of each round segment
   int64_t* first;      // [p][kcap] first accepted sample inside each segment (0: none)
+  int2* plist;         // [p*kcap] (chain, segment) work list of the prefix pass
   int ck_C;            // sweeps per segment in the current round
   int ck_K;            // segments in the current round
   int kcap;            // segment capacity
@@ -58,7 +59,11 @@ enum StatIndex : int {
   kStatSearched = 6,     // samples replayed by the last joint's searches
   kStatJoinedTotal = 7,  // samples kept by all joints of the job
   kStatPending = 8,      // chains queued for the current resolution pass
-  kStatCount = 12
+  kStatWholeFill = 9,    // running position while the prefix work list is filled
+  kStatQueueSearch = 11, // next work item of the running persistent pass
+  kStatQueuePrefix = 10, // work items of the prefix pass
+  kStatPartial = 12,     // partial-segment items of the prefix pass (listed after the whole ones)
+  kStatCount = 13
 };
 
 // ---- kernels (mc_kernels.cu) ----
@@ -72,10 +77,12 @@ cudaError_t k_join(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S
                    bool naive, cudaStream_t st);
 
 // pieces of the joint shared by all lattice sizes
-constexpr int kGridPasses = 6;  // grid-wide resolution passes before the one-block fallback
+constexpr int kGridPasses = 10;  // grid-wide resolution passes before the one-block fallback
 cudaError_t join_prelude(const DevJob& j, cudaStream_t st);
 cudaError_t join_mark(const DevJob& j, cudaStream_t st);
 cudaError_t join_select(const DevJob& j, bool listed, cudaStream_t st);
+cudaError_t join_prefix_list(const DevJob& j, cudaStream_t st);
+cudaError_t join_reset_queue(const DevJob& j, cudaStream_t st);
 cudaError_t join_finalize(const DevJob& j, int64_t S, cudaStream_t st);
 
 // per-unit launchers of the templated chain kernels (mc_inst_*.cu)

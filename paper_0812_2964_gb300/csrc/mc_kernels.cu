@@ -172,12 +172,20 @@ __global__ void naive_kernel(const DevJob j) {
 }
 
 __global__ void clear_stats_kernel(const DevJob j) {
-  if (threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     j.stats[kStatSearched] = 0;
     j.stats[kStatMismatch] = 0;
     j.stats[kStatPasses] = 0;
     j.stats[kStatPending] = 0;
+    j.stats[kStatQueuePrefix] = 0;
+    j.stats[kStatPartial] = 0;
+    j.stats[kStatWholeFill] = 0;
   }
+  // first accepted sample per segment: -1 = not searched yet
+  const long long n = static_cast<long long>(j.p) * j.kcap;
+  for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < n;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x)
+    j.first[idx] = -1;
 }
 
 // One grid-wide resolution pass, part 1 (one block): with the current k's,
@@ -198,6 +206,7 @@ __global__ void __launch_bounds__(1024) mark_kernel(const DevJob j) {
     if (x != j.xused[i]) {
       j.xused[i] = x;
       j.k[i] = -1;
+      for (int s2 = 0; s2 < j.ck_K; ++s2) j.first[static_cast<size_t>(i) * j.kcap + s2] = -1;
       j.work[atomicAdd(&s_count, 1)] = i;
     }
   }
@@ -247,9 +256,25 @@ LaunchShape default_shape(int L, int p, int num_sms) {
   return s;
 }
 
+// The joint's replay kernels use full warps whatever shape generation runs
+// with (their work items are (chain, segment) pairs, not chains): 32 items a
+// warp, as many warps a block as fit, preferring a shape whose threshold
+// table and histogram still fit in shared memory.
+static LaunchShape join_shape(int L, const LaunchShape& gen) {
+  LaunchShape best = gen;
+  bool have = false;
+  for (int w = 4; w >= 1; w >>= 1) {
+    LaunchShape s{gen.placement, 32, w};
+    if (!shape_supported(L, s)) continue;
+    if (table_fits(L, s, true)) return s;
+    if (!have) best = s, have = true;
+  }
+  return best;
+}
+
 cudaError_t join_prelude(const DevJob& j, cudaStream_t st) {
   spec_inputs_kernel<<<blocks_for(j.p, 256), 256, 0, st>>>(j);
-  clear_stats_kernel<<<1, 32, 0, st>>>(j);
+  clear_stats_kernel<<<256, 256, 0, st>>>(j);
   tj_kernel<<<blocks_for(static_cast<long long>(j.p) * j.np1, 256), 256, 0, st>>>(j, nullptr, j.p);
   launches_add(3);
   return cudaGetLastError();
@@ -269,6 +294,62 @@ __global__ void select_kernel(const DevJob j, const int listed) {
       break;
     }
   j.k[i] = k;
+}
+
+// Work list of the prefix pass: for every chain, its whole segments before
+// the one holding k_i (all segments if nothing is kept) and, if k_i is not
+// the first sample of its segment, that segment as a partial item.  Whole
+// segments are counted first, then placed at the front of the list.
+__global__ void prefix_count_kernel(const DevJob j, const int64_t S) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= j.p) return;
+  const int64_t segN = static_cast<int64_t>(j.ck_C) * j.N;
+  const int64_t k = j.k[i];
+  const int whole = (k > 0) ? static_cast<int>((k - 1) / segN) : j.ck_K;
+  atomicAdd(reinterpret_cast<unsigned long long*>(&j.stats[kStatQueuePrefix]), static_cast<unsigned long long>(whole));
+  (void)S;
+}
+
+__global__ void prefix_fill_kernel(const DevJob j, const int64_t S) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= j.p) return;
+  const int64_t segN = static_cast<int64_t>(j.ck_C) * j.N;
+  const int64_t k = j.k[i];
+  const int whole = (k > 0) ? static_cast<int>((k - 1) / segN) : j.ck_K;
+  unsigned long long* w = reinterpret_cast<unsigned long long*>(&j.stats[kStatWholeFill]);
+  unsigned long long* pcount = reinterpret_cast<unsigned long long*>(&j.stats[kStatPartial]);
+  if (whole > 0) {
+    const unsigned long long pos = atomicAdd(w, static_cast<unsigned long long>(whole));
+    for (int s = 0; s < whole; ++s) j.plist[pos + s] = make_int2(i, s);
+  }
+  if (k > 0 && (k - 1) % segN != 0) {
+    const unsigned long long total_whole = static_cast<unsigned long long>(j.stats[kStatQueuePrefix]);
+    const unsigned long long pos = total_whole + atomicAdd(pcount, 1ull);
+    j.plist[pos] = make_int2(i, whole);
+  }
+  (void)S;
+}
+
+__global__ void prefix_total_kernel(const DevJob j) {
+  if (threadIdx.x == 0) j.stats[kStatQueuePrefix] += j.stats[kStatPartial];
+}
+
+__global__ void reset_queue_kernel(const DevJob j) {
+  if (threadIdx.x == 0) j.stats[kStatQueueSearch] = 0;
+}
+
+cudaError_t join_reset_queue(const DevJob& j, cudaStream_t st) {
+  reset_queue_kernel<<<1, 32, 0, st>>>(j);
+  launches_add(1);
+  return cudaGetLastError();
+}
+
+cudaError_t join_prefix_list(const DevJob& j, cudaStream_t st) {
+  prefix_count_kernel<<<blocks_for(j.p, 256), 256, 0, st>>>(j, 0);
+  prefix_fill_kernel<<<blocks_for(j.p, 256), 256, 0, st>>>(j, 0);
+  prefix_total_kernel<<<1, 32, 0, st>>>(j);
+  launches_add(3);
+  return cudaGetLastError();
 }
 
 cudaError_t join_select(const DevJob& j, bool listed, cudaStream_t st) {
@@ -326,7 +407,7 @@ cudaError_t k_join(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S
     launches_add(2);
     return cudaGetLastError();
   }
-  return dispatch(j, s, false, t0, S, false, r, st);
+  return dispatch(j, join_shape(j.L, s), false, t0, S, false, r, st);
 }
 
 cudaError_t k_init_lattice(const DevJob& j, int start, cudaStream_t st) {

@@ -24,3 +24,4 @@ inline double __longlong_as_double(long long v) { double d; memcpy(&d, &v, 8); r
 inline long long __double_as_longlong(double d) { long long v; memcpy(&v, &d, 8); return v; }
 template <class T, class U> inline T atomicAdd(T* p, U v) { T o = *p; *p = o + (T)v; return o; }
 inline size_t __cvta_generic_to_shared(const void* p) { return (size_t)p; }
+template <class T> inline T __ldg(const T* p) { return *p; }
