@@ -398,6 +398,75 @@ def run_batch(args):
     return 0
 
 
+def run_serving(args):
+    """Serving: a Poisson stream of weight-estimation jobs (L in {16, ..., 128},
+    256-4096 chains, 20-60 iterations) submitted at their arrival times to
+    the continuous-batching server (40 GB budget); value = kept samples of
+    all jobs / makespan (first arrival to last completion); p50/p99 of the
+    job latency (arrival to W ready)."""
+    import torch
+
+    import paper_0812_2964_gb300 as mc
+    from paper_0812_2964_gb300.workloads import serving_stream
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    mc.build()
+    S = args.sweeps or 20
+    stream = serving_stream(args.jobs, rate=args.rate, sweeps=S)
+    budget = 40 << 30
+    # warm-up: one small job of every size (module load, first launches)
+    with mc.Server(budget, args.slots) as srv:
+        for i, L in enumerate((16, 32, 48, 64, 96, 128)):
+            srv.wait(srv.submit(L, 256, 99 + i, 2, S))
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    l0 = mc.mc_kernel_launches()
+    with mc.Server(budget, args.slots) as srv:
+        ids = []
+        t_base = srv.clock()
+        for job in stream:
+            delay = t_base + job.arrival - srv.clock()
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(job.L, job.chains, job.seed + rank, job.iterations, job.sweeps))
+        res = [srv.wait(j) for j in ids]
+        info = srv.info()
+    launches = mc.mc_kernel_launches() - l0
+    clk = clocks.stop()
+    st = [r[1] for r in res]
+    lat = np.array([s["t_done"] - s["t_submit"] for s in st])
+    qwait = np.array([s["t_admit"] - s["t_submit"] for s in st])
+    t_first = min(s["t_submit"] for s in st)
+    t_last = max(s["t_done"] for s in st)
+    span = t_last - t_first
+    joined = sum(s["joined"] for s in st)
+    attempts = sum(s["attempts"] for s in st)
+    offered = attempts / max(1e-9, stream[-1].arrival - stream[0].arrival)
+    d2h = sum((j.L * j.L + 1) * 8 for j in stream)
+    value = joined / span
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(stream),
+            "warmup": 6, "ms_per_step": 1e3 * span / len(stream), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "serving", "jobs": len(stream), "rate_jobs_per_s": args.rate,
+                       "arrival_seed": 5, "sizes": [16, 32, 48, 64, 96, 128], "chains": "256..4096 step 256",
+                       "iterations": "20..60", "sweeps_per_iteration": S, "budget_bytes": budget,
+                       "slots": args.slots, "step": "one job (arrival to W ready)"},
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(lat.mean()), "max": float(lat.max())},
+            "queue_wait_s": {"p50": float(np.percentile(qwait, 50)), "p99": float(np.percentile(qwait, 99))},
+            "raw_attempts_per_s": attempts / span, "offered_attempts_per_s": offered,
+            "utilisation_proxy": offered / (attempts / span),
+            "server": {k: info[k] for k in ("peak_active", "peak_bytes", "admitted", "completed")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h / len(stream),
+                    "note": "host-timed from submission to collection; each job's input is its spec"},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -405,17 +474,22 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", default=WORKLOAD,
-                    help="L32_p16384 (default), L64_p4096, L128_p1024, L8_p64, or batch_uneven")
+                    help="L32_p16384 (default), L64_p4096, L128_p1024, L8_p64, batch_uneven or serving")
     ap.add_argument("--sweeps", type=int, default=0, help="override sweeps per iteration")
     ap.add_argument("--tune", action="store_true", help="pick the launch shape with mc_autotune first")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--jobs", type=int, default=400, help="serving: jobs in the arrival stream")
+    ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
+    ap.add_argument("--slots", type=int, default=32, help="serving: server slots")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch_uneven":
         return run_batch(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_gpu(args)
 
 

@@ -67,6 +67,7 @@ typedef struct mc_info {
   int placement;               /* 0: lattice in registers, 1: in shared memory */
   int chains_per_warp, warps_per_block;
   size_t device_bytes;         /* device memory held by the job */
+  int64_t last_scanned;        /* chains the exact scan settled (0: speculation sufficed) */
 } mc_info;
 
 /* Create a job: Sec. 2 step 1 (h = 0, initial configurations C_1) and

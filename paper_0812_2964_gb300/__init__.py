@@ -21,7 +21,9 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_get_table", "mc_get_spins", "mc_set_spins", "mc_get_energies", "mc_get_trace",
     "mc_get_trace_chain",
     "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error",
-    "mc_generate_noalloc", "mc_autotune", "mc_batch_run"]
+    "mc_generate_noalloc", "mc_autotune", "mc_batch_run",
+    "mc_job_device_bytes", "mc_server_create", "mc_server_submit", "mc_server_poll", "mc_server_wait",
+    "mc_server_get_info", "mc_server_clock", "mc_server_free", "Server"]
 
 # revision of the generation kernel; bump when it changes (profiles record it)
 KERNEL_REV = "gen-2"
@@ -48,7 +50,31 @@ class mc_info(ctypes.Structure):
                 ("last_searched", ctypes.c_int64), ("total_joined", ctypes.c_int64),
                 ("placement", ctypes.c_int),
                 ("chains_per_warp", ctypes.c_int), ("warps_per_block", ctypes.c_int),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("last_scanned", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class mc_jobspec(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("n_chains", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("start", ctypes.c_int), ("iterations", ctypes.c_int), ("sweeps", ctypes.c_int64)]
+
+
+class mc_jobstats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("slot", ctypes.c_int), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("attempts", ctypes.c_int64),
+                ("joined", ctypes.c_int64), ("device_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class mc_server_info(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int), ("queued", ctypes.c_int), ("active", ctypes.c_int),
+                ("finished", ctypes.c_int), ("budget_bytes", ctypes.c_uint64),
+                ("bytes_in_use", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
+                ("peak_active", ctypes.c_int), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -97,6 +123,15 @@ def lib():
             "mc_generate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                                    ctypes.c_uint64, ctypes.c_int64, _vp, _vp, _vp,
                                                    _vp, _vp]),
+            "mc_job_device_bytes": (ctypes.c_uint64, [ctypes.c_int, ctypes.c_int, ctypes.c_int64]),
+            "mc_server_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(_vp)]),
+            "mc_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(mc_jobspec), ctypes.POINTER(ctypes.c_uint64)]),
+            "mc_server_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+            "mc_server_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, ctypes.c_int,
+                                              ctypes.POINTER(mc_jobstats)]),
+            "mc_server_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(mc_server_info)]),
+            "mc_server_clock": (ctypes.c_double, [_vp]),
+            "mc_server_free": (None, [_vp]),
             "mc_kernel_launches": (ctypes.c_uint64, []),
             "mc_last_error": (ctypes.c_char_p, []),
         }
@@ -368,3 +403,93 @@ class Job:
 
     def sync(self):
         mc_sync(self.h)
+
+
+# ------------------------------------------------------------ serving
+def mc_job_device_bytes(L: int, n_chains: int, sweeps: int) -> int:
+    return int(lib().mc_job_device_bytes(L, n_chains, sweeps))
+
+
+def mc_server_create(budget_bytes: int, max_slots: int):
+    h = _vp()
+    _check(lib().mc_server_create(budget_bytes, max_slots, ctypes.byref(h)))
+    return h
+
+
+def mc_server_submit(srv, L: int, n_chains: int, seed: int, start: int, iterations: int, sweeps: int) -> int:
+    spec = mc_jobspec(L, n_chains, seed, start, iterations, sweeps)
+    jid = ctypes.c_uint64()
+    _check(lib().mc_server_submit(srv, ctypes.byref(spec), ctypes.byref(jid)))
+    return jid.value
+
+
+def mc_server_poll(srv, jid: int) -> bool:
+    done = ctypes.c_int()
+    _check(lib().mc_server_poll(srv, jid, ctypes.byref(done)))
+    return bool(done.value)
+
+
+def mc_server_wait(srv, jid: int, n_levels: int | None):
+    """Block until job jid is done; returns (W or None, stats dict).  Raises
+    McError with the job's own status if it failed."""
+    st = mc_jobstats()
+    W = np.zeros(n_levels, np.float64) if n_levels else None
+    rc = lib().mc_server_wait(srv, jid, _ptr(W) if W is not None else None, n_levels or 0, ctypes.byref(st))
+    _check(rc)
+    return W, st.as_dict()
+
+
+def mc_server_get_info(srv) -> dict:
+    info = mc_server_info()
+    _check(lib().mc_server_get_info(srv, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def mc_server_clock(srv) -> float:
+    return float(lib().mc_server_clock(srv))
+
+
+def mc_server_free(srv):
+    lib().mc_server_free(srv)
+
+
+class Server:
+    """Continuous-batching server for weight-estimation jobs (numpy out)."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 16):
+        self.h = mc_server_create(budget_bytes, max_slots)
+        self._levels = {}
+
+    def submit(self, L: int, n_chains: int, seed: int, iterations: int, sweeps: int, start: int = 1) -> int:
+        jid = mc_server_submit(self.h, L, n_chains, seed, start, iterations, sweeps)
+        self._levels[jid] = L * L + 1
+        return jid
+
+    def poll(self, jid: int) -> bool:
+        return mc_server_poll(self.h, jid)
+
+    def wait(self, jid: int):
+        return mc_server_wait(self.h, jid, self._levels.pop(jid))
+
+    def clock(self) -> float:
+        return mc_server_clock(self.h)
+
+    def info(self) -> dict:
+        return mc_server_get_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            mc_server_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libmcgpu.so")
 SOURCES = ["mc_kernels.cu", "mc_api.cu", "mc_inst_reg_a.cu", "mc_inst_reg_b.cu", "mc_inst_reg_c.cu",
            "mc_inst_smem_1.cu", "mc_inst_smem_2.cu", "mc_inst_smem_3.cu", "mc_inst_smem_4.cu",
            "mc_inst_smem_48.cu", "mc_inst_smem_64.cu", "mc_inst_smem_96.cu", "mc_inst_smem_100.cu",
-           "mc_inst_smem_128.cu", "mc_noalloc.cu", "mc_batch.cu"]
+           "mc_inst_smem_128.cu", "mc_noalloc.cu", "mc_batch.cu", "mc_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -40,7 +40,7 @@ def flags(verbose_ptxas: bool = False) -> list[str]:
 
 
 def _deps() -> list[str]:
-    out = [os.path.join(ROOT, "include", "mc.h"), __file__]
+    out = [os.path.join(ROOT, "include", n) for n in os.listdir(os.path.join(ROOT, "include"))] + [__file__]
     for n in os.listdir(CSRC):
         out.append(os.path.join(CSRC, n))
     return out

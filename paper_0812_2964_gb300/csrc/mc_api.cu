@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/mc.h"
+#include "../../include/mc_server.h"
 #include "mc_batch.h"
 #include "mc_internal.h"
 
@@ -69,12 +70,24 @@ struct mc_job {
 
 namespace {
 
+// Device memory of a job comes from the device's stream-ordered pool
+// (cudaMallocAsync / cudaFreeAsync on the job's stream): freeing a job does
+// not wait for work of other jobs, which a server running many jobs at once
+// relies on.  The pool keeps freed memory for later jobs.
+void raw_free(mc_job* j, void* v) {
+  if (v) cudaFreeAsync(v, j->stream);
+}
+
+cudaError_t raw_alloc(mc_job* j, void** v, size_t bytes) {
+  return cudaMallocAsync(v, bytes ? bytes : 1, j->stream);
+}
+
 template <class T>
 int dalloc(mc_job* j, T** p, size_t count) {
   void* v = nullptr;
   const size_t b = sizeof(T) * (count ? count : 1);
-  cudaError_t e = cudaMalloc(&v, b);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  cudaError_t e = raw_alloc(j, &v, b);
+  if (e != cudaSuccess) return cuda_fail(e, "device allocation");
   j->allocs.push_back(v);
   j->bytes += b;
   *p = static_cast<T*>(v);
@@ -82,20 +95,37 @@ int dalloc(mc_job* j, T** p, size_t count) {
 }
 
 void free_all(mc_job* j) {
-  for (void* v : j->allocs) cudaFree(v);
+  if (j->stream) {
+    for (void* v : j->allocs) raw_free(j, v);
+    raw_free(j, j->d.ckpt);
+    raw_free(j, j->d.ckm);
+    raw_free(j, j->d.first);
+    raw_free(j, j->d.plist);
+    raw_free(j, j->d.trace);
+  }
   j->allocs.clear();
-  if (j->d.ckpt) cudaFree(j->d.ckpt);
-  if (j->d.ckm) cudaFree(j->d.ckm);
-  if (j->d.first) cudaFree(j->d.first);
-  if (j->d.plist) cudaFree(j->d.plist);
   j->d.plist = nullptr;
   j->d.ckpt = nullptr;
   j->d.ckm = nullptr;
   j->d.first = nullptr;
-  if (j->d.trace) cudaFree(j->d.trace);
   j->d.trace = nullptr;
   if (j->own_stream) cudaStreamDestroy(j->own_stream);
   j->own_stream = nullptr;
+  j->stream = nullptr;
+}
+
+// Once per device: the pool behind raw_alloc keeps what jobs free.
+cudaError_t pool_setup(int device) {
+  static std::mutex mu;
+  static std::vector<int> done;
+  std::lock_guard<std::mutex> lk(mu);
+  if (std::find(done.begin(), done.end(), device) != done.end()) return cudaSuccess;
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = cudaDeviceGetDefaultMemPool(&pool, device);
+  uint64_t keep = ~0ull;
+  if (e == cudaSuccess) e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  if (e == cudaSuccess) done.push_back(device);
+  return e;
 }
 
 int check_job(mc_job* j) {
@@ -133,6 +163,7 @@ int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
   int rc = MC_OK;
   cudaError_t e = cudaGetDevice(&j->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&j->num_sms, cudaDevAttrMultiProcessorCount, j->device);
+  if (e == cudaSuccess) e = pool_setup(j->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&j->own_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     rc = cuda_fail(e, "device setup");
@@ -158,7 +189,7 @@ int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
       (rc = dalloc(j, &d.k, n_chains)) ||
       (rc = dalloc(j, &d.xused, n_chains)) || (rc = dalloc(j, &d.tj, static_cast<size_t>(n_chains) * np1)) ||
       (rc = dalloc(j, &d.offsets, n_chains)) || (rc = dalloc(j, &d.work, n_chains)) ||
-      (rc = dalloc(j, &d.lastacc, n_chains)) ||
+      (rc = dalloc(j, &d.lastacc, n_chains)) || (rc = dalloc(j, &d.summ, 3ull * n_chains)) ||
       (rc = dalloc(j, &d.stats, mcgpu::kStatCount))) {
     free_all(j);
     delete j;
@@ -223,13 +254,20 @@ namespace {
 
 // Segments of a round for the joint's parallel replays: at least 32 (or S),
 // and at most 2^24 samples each (the prefix pass relies on that bound).
-void round_segments(const mc_job* job, int64_t n_sweeps, int* K, int* C) {
-  const int64_t M = n_sweeps * job->N;
+void round_segments(int N, int64_t n_sweeps, int* K, int* C) {
+  const int64_t M = n_sweeps * N;
   int64_t k = std::max<int64_t>(32, (M + (int64_t(1) << 24) - 1) >> 24);
   k = std::min<int64_t>(k, n_sweeps);
   const int64_t c = (n_sweeps + k - 1) / k;
   *C = static_cast<int>(c);
   *K = static_cast<int>((n_sweeps + c - 1) / c);
+}
+
+// Bytes of the checkpoint buffers for K segments: lattices, levels, first
+// accepted sample per segment, prefix work list.
+size_t segment_bytes(const mc_job* job, int K) {
+  const size_t lw = static_cast<size_t>(job->L) * job->wd;
+  return static_cast<size_t>(K) * job->p * (lw * 4 + 4 + 8 + 8);
 }
 
 // Checkpoint buffers for at least K segments.
@@ -239,12 +277,11 @@ int ensure_segments(mc_job* job, int K) {
   const size_t lw = static_cast<size_t>(job->L) * job->wd;
   const size_t p = static_cast<size_t>(job->p);
   if (d.ckpt) {
-    cudaStreamSynchronize(job->stream);
-    cudaFree(d.ckpt);
-    cudaFree(d.ckm);
-    cudaFree(d.first);
-    cudaFree(d.plist);
-    job->bytes -= static_cast<size_t>(d.kcap) * p * (lw * 4 + 4 + 8 + 8);
+    raw_free(job, d.ckpt);
+    raw_free(job, d.ckm);
+    raw_free(job, d.first);
+    raw_free(job, d.plist);
+    job->bytes -= segment_bytes(job, d.kcap);
     d.ckpt = nullptr;
     d.ckm = nullptr;
     d.first = nullptr;
@@ -252,15 +289,15 @@ int ensure_segments(mc_job* job, int K) {
     d.kcap = 0;
   }
   void *a = nullptr, *b = nullptr, *c = nullptr, *w = nullptr;
-  cudaError_t e = cudaMalloc(&a, static_cast<size_t>(K) * lw * p * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&b, static_cast<size_t>(K) * p * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&c, static_cast<size_t>(K) * p * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&w, static_cast<size_t>(K) * p * 8);
+  cudaError_t e = raw_alloc(job, &a, static_cast<size_t>(K) * lw * p * 4);
+  if (e == cudaSuccess) e = raw_alloc(job, &b, static_cast<size_t>(K) * p * 4);
+  if (e == cudaSuccess) e = raw_alloc(job, &c, static_cast<size_t>(K) * p * 8);
+  if (e == cudaSuccess) e = raw_alloc(job, &w, static_cast<size_t>(K) * p * 8);
   if (e != cudaSuccess) {
-    if (a) cudaFree(a);
-    if (b) cudaFree(b);
-    if (c) cudaFree(c);
-    if (w) cudaFree(w);
+    raw_free(job, a);
+    raw_free(job, b);
+    raw_free(job, c);
+    raw_free(job, w);
     return cuda_fail(e, "checkpoint allocation");
   }
   d.ckpt = static_cast<uint32_t*>(a);
@@ -268,7 +305,7 @@ int ensure_segments(mc_job* job, int K) {
   d.first = static_cast<int64_t*>(c);
   d.plist = static_cast<int2*>(w);
   d.kcap = K;
-  job->bytes += static_cast<size_t>(K) * p * (lw * 4 + 4 + 8 + 8);
+  job->bytes += segment_bytes(job, K);
   return MC_OK;
 }
 
@@ -278,14 +315,13 @@ int ensure_trace(mc_job* job, int64_t n_sweeps) {
   const size_t need = static_cast<size_t>(n_sweeps) * job->p;
   if (need <= job->trace_cap) return MC_OK;
   if (d.trace) {
-    cudaStreamSynchronize(job->stream);
-    cudaFree(d.trace);
+    raw_free(job, d.trace);
     job->bytes -= job->trace_cap * sizeof(int32_t);
     d.trace = nullptr;
     job->trace_cap = 0;
   }
   void* v = nullptr;
-  MC_CUDA(cudaMalloc(&v, need * sizeof(int32_t)), "trace allocation");
+  MC_CUDA(raw_alloc(job, &v, need * sizeof(int32_t)), "trace allocation");
   d.trace = static_cast<int32_t*>(v);
   job->trace_cap = need;
   job->bytes += need * sizeof(int32_t);
@@ -303,7 +339,7 @@ int round_prepare(mc_job* job, int64_t n_sweeps, uint64_t* t0) {
   if (job->trace_on)
     if (int rc = ensure_trace(job, n_sweeps)) return rc;
   int K = 0, C = 0;
-  round_segments(job, n_sweeps, &K, &C);
+  round_segments(job->N, n_sweeps, &K, &C);
   if (int rc = ensure_segments(job, K)) return rc;
   DevJob& d = job->d;
   d.ck_K = K;
@@ -414,7 +450,7 @@ int mc_batch_run(mc_job** jobs, int n_jobs, int iterations, int64_t n_sweeps, in
   for (int i = 0; i < n_jobs && rc == MC_OK; ++i) {  // no allocation inside a capture
     if (jobs[i]->trace_on) rc = ensure_trace(jobs[i], n_sweeps);
     int K = 0, C = 0;
-    round_segments(jobs[i], n_sweeps, &K, &C);
+    round_segments(jobs[i]->N, n_sweeps, &K, &C);
     if (rc == MC_OK) rc = ensure_segments(jobs[i], K);
   }
   bool capturing = false;
@@ -596,6 +632,7 @@ int mc_get_info(mc_job* job, mc_info* info) {
   info->chains_per_warp = job->shape.cpw;
   info->warps_per_block = job->shape.wpb;
   info->device_bytes = job->bytes;
+  info->last_scanned = st[mcgpu::kStatScanned];
   return MC_OK;
 }
 
@@ -695,6 +732,19 @@ int mc_autotune(mc_job* job, int64_t probe_sweeps, int use_cache, int* placement
   if (cpw) *cpw = best.cpw;
   if (wpb) *wpb = best.wpb;
   return MC_OK;
+}
+
+uint64_t mc_job_device_bytes(int L, int n_chains, int64_t sweeps) {
+  if (L < 4 || L > 128 || (L % 4) != 0 || n_chains < 1 || sweeps < 1) return 0;
+  const uint64_t N = static_cast<uint64_t>(L) * L, np1 = N + 1, wd = (L + 31) / 32;
+  const uint64_t p = static_cast<uint64_t>(n_chains), lw = static_cast<uint64_t>(L) * wd, lat = p * lw;
+  // as allocated by mc_init: spins, spins0, m, m0, W, T, h, hgen, dpre, k,
+  // xused, tj, offsets, work, lastacc, summ, stats
+  uint64_t b = lat * 4 * 2 + p * 4 * 2 + np1 * 8 + 5 * np1 * 4 + np1 * 8 * 3 + p * 8 + p * 4 + p * np1 * 4 +
+               p * 8 + p * 4 + p * 4 + p * 12 + mcgpu::kStatCount * 8;
+  int K = 0, C = 0;
+  round_segments(L * L, sweeps, &K, &C);
+  return b + static_cast<uint64_t>(K) * p * (lw * 4 + 4 + 8 + 8);
 }
 
 int mc_sync(mc_job* job) {

@@ -246,4 +246,42 @@ struct SearchHook {
   }
 };
 
+// Summary replay (exact joint resolution, Sec. 2 step 4): over the samples
+// of a segment, the smallest joint uniform seen at each level, folded into
+// the chain's row with atomicMin once per run of equal levels; also the
+// range of levels visited and whether some run's minimum was 0xFFFFFFFF.
+struct SummaryHook {
+  uint32_t* umin;  // row of the chain, indexed by level
+  int64_t k;
+  uint32_t chain, r, k0, k1;
+  uint4 jr;
+  int cur, lo, hi;
+  uint32_t run_min;
+  bool flag;
+  bool done;       // never set: the whole segment is summarised
+  __device__ __forceinline__ void sample(int m4) {
+    const int m = m4 >> 2;
+    ++k;
+    const uint64_t q = static_cast<uint64_t>(k - 1);
+    if ((q & 3u) == 0u)
+      jr = philox4x32_10(make_uint4(static_cast<uint32_t>(q >> 2), r, chain, kTagJoint), k0, k1);
+    const uint32_t u = uint4_word(jr, static_cast<uint32_t>(q & 3u));
+    if (m != cur) {
+      flush();
+      cur = m;
+      run_min = u;
+    } else {
+      run_min = min(run_min, u);
+    }
+  }
+  __device__ __forceinline__ void flush() {
+    if (cur >= 0) {
+      atomicMin(&umin[cur], run_min);
+      flag = flag || (run_min == 0xFFFFFFFFu);
+      lo = min(lo, cur);
+      hi = max(hi, cur);
+    }
+  }
+};
+
 }  // namespace mcgpu

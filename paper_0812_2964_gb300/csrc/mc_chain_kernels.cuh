@@ -333,6 +333,59 @@ __global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int c
     atomicAdd(reinterpret_cast<unsigned long long*>(&j.stats[kStatSearched]), static_cast<unsigned long long>(searched));
 }
 
+// Summary replay for the exact scan: work items (chain, segment) for the
+// chains from the first pending one on, all segments; persistent warps take
+// cpw consecutive items at a time, as in search_kernel.  Nothing happens
+// when no chain is pending.
+template <class Factory, bool TSMEM>
+__global__ void __launch_bounds__(128) summary_kernel(const DevJob j, const int cpw, const uint64_t t0,
+                                                      const int64_t S, const uint32_t r) {
+  if (j.stats[kStatPending] == 0) return;
+  const int f = static_cast<int>(j.stats[kStatFirstPending]);
+  const int nchains = j.p - f;
+  const long long items = static_cast<long long>(nchains) * j.ck_K;
+  const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, false);
+  BlockCtx b = block_setup<TSMEM>(j, sp, cpw, 0, false);
+  __syncthreads();
+  unsigned long long* queue = reinterpret_cast<unsigned long long*>(&j.stats[kStatQueueSearch]);
+  long long searched = 0;
+  for (;;) {
+    long long base = 0;
+    if (b.lane == 0) base = static_cast<long long>(atomicAdd(queue, static_cast<unsigned long long>(cpw)));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (base >= items) break;
+    const long long item = base + b.lane;
+    if (b.lane < cpw && item < items) {
+      const int seg = static_cast<int>(item / nchains);
+      const int i = f + static_cast<int>(item % nchains);
+      SummaryHook hk;
+      hk.umin = j.tj + static_cast<size_t>(i) * j.np1;
+      hk.k = static_cast<int64_t>(seg) * j.ck_C * j.N;
+      hk.chain = static_cast<uint32_t>(i);
+      hk.r = r;
+      hk.k0 = j.key0;
+      hk.k1 = j.key1;
+      hk.jr = make_uint4(0u, 0u, 0u, 0u);
+      hk.cur = -1;
+      hk.lo = 0x7FFFFFFF;
+      hk.hi = -1;
+      hk.run_min = 0xFFFFFFFFu;
+      hk.flag = false;
+      hk.done = false;
+      const int64_t k_begin = hk.k;
+      replay_segment<Factory>(j, b, i, seg, t0, S, hk);
+      hk.flush();
+      atomicMin(&j.summ[i], hk.lo);
+      atomicMax(&j.summ[j.p + i], hk.hi);
+      if (hk.flag) atomicOr(&j.summ[2 * j.p + i], 1);
+      searched += hk.k - k_begin;
+    }
+    __syncwarp();
+  }
+  if (searched)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&j.stats[kStatSearched]), static_cast<unsigned long long>(searched));
+}
+
 struct PrefixHook {
   uint32_t* hist;
   int64_t k, cut;  // samples with index < cut are counted
@@ -592,14 +645,46 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
   if ((e = join_reset_queue(j, st)) != cudaSuccess) return e;
   kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, 0);
   if ((e = join_select(j, false, st)) != cudaSuccess) return e;
-  // grid-wide resolution passes (the listed chains' items fit in grid_all)
-  for (int pass = 0; pass < kGridPasses; ++pass) {
-    if ((e = join_mark(j, st)) != cudaSuccess) return e;
+  // grid-wide speculative resolution passes
+  auto pass = [&](int n) -> cudaError_t {
+    for (int q = 0; q < n; ++q) {
+      cudaError_t e2 = join_mark(j, st);
+      if (e2 == cudaSuccess) e2 = join_reset_queue(j, st);
+      if (e2 != cudaSuccess) return e2;
+      kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, 1);
+      launches_add(1);
+      if ((e2 = join_select(j, true, st)) != cudaSuccess) return e2;
+    }
+    return cudaSuccess;
+  };
+  const bool exact_scan = static_cast<long long>(j.p) * S * j.N <= kScanMaxSamples;
+  if (exact_scan) {
+    // a few speculative passes; if chains are still pending, the summary
+    // replay and the exact scan settle every input, one search pass finds
+    // the new k's, and the ordinary passes catch what the scan left
+    if ((e = pass(kGridPassesScan)) != cudaSuccess) return e;
+    if ((e = join_mark(j, st, false)) != cudaSuccess) return e;
+    if ((e = join_summary_init(j, st)) != cudaSuccess) return e;
+    if ((e = join_reset_queue(j, st)) != cudaSuccess) return e;
+    auto ks = summary_kernel<F, TS>;
+    if ((e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=
+        cudaSuccess)
+      return e;
+    const unsigned grid_sum = static_cast<unsigned>(
+        std::min<long long>(blocks_for(items, per_block), resident_blocks(ks, 32 * s.wpb, bytes)));
+    ks<<<grid_sum, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r);
+    launches_add(1);
+    if ((e = join_scan(j, st)) != cudaSuccess) return e;
+    if ((e = join_tj_list(j, st)) != cudaSuccess) return e;
     if ((e = join_reset_queue(j, st)) != cudaSuccess) return e;
     kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, 1);
+    launches_add(1);
     if ((e = join_select(j, true, st)) != cudaSuccess) return e;
+    if ((e = pass(kGridPassesScan)) != cudaSuccess) return e;
+  } else {
+    if ((e = pass(kGridPasses)) != cudaSuccess) return e;
   }
-  launches_add(1 + kGridPasses);
+  launches_add(1);
   auto kr = resolve_kernel<F, TS>;
   if ((e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=
       cudaSuccess)

@@ -43,6 +43,7 @@ struct DevJob {
   int32_t* ckm;        // [kcap][p] level at the start of each round segment
   int64_t* first;      // [p][kcap] first accepted sample inside each segment (0: none)
   int2* plist;         // [p*kcap] (chain, segment) work list of the prefix pass
+  int32_t* summ;       // [3][p] summary pass: lowest and highest level visited, flag
   int ck_C;            // sweeps per segment in the current round
   int ck_K;            // segments in the current round
   int kcap;            // segment capacity
@@ -63,7 +64,9 @@ enum StatIndex : int {
   kStatQueueSearch = 11, // next work item of the running persistent pass
   kStatQueuePrefix = 10, // work items of the prefix pass
   kStatPartial = 12,     // partial-segment items of the prefix pass (listed after the whole ones)
-  kStatCount = 13
+  kStatFirstPending = 13,// lowest chain queued by the last mark pass (p if none)
+  kStatScanned = 14,     // chains whose input the exact scan settled (last joint)
+  kStatCount = 15
 };
 
 // ---- kernels (mc_kernels.cu) ----
@@ -77,13 +80,22 @@ cudaError_t k_join(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S
                    bool naive, cudaStream_t st);
 
 // pieces of the joint shared by all lattice sizes
-constexpr int kGridPasses = 10;  // grid-wide resolution passes before the one-block fallback
+// grid-wide speculative resolution passes: before the exact scan (when the
+// round is short enough for the summary replay), and without it
+constexpr int kGridPassesScan = 2;
+constexpr int kGridPasses = 10;
+// rounds with at most this many samples (all chains) take the summary replay
+// and the exact scan when speculation has not settled after kGridPassesScan
+constexpr long long kScanMaxSamples = 20000000000ll;
 cudaError_t join_prelude(const DevJob& j, cudaStream_t st);
-cudaError_t join_mark(const DevJob& j, cudaStream_t st);
+cudaError_t join_mark(const DevJob& j, cudaStream_t st, bool thresholds = true);
+cudaError_t join_tj_list(const DevJob& j, cudaStream_t st);
 cudaError_t join_select(const DevJob& j, bool listed, cudaStream_t st);
 cudaError_t join_prefix_list(const DevJob& j, cudaStream_t st);
 cudaError_t join_reset_queue(const DevJob& j, cudaStream_t st);
 cudaError_t join_finalize(const DevJob& j, int64_t S, cudaStream_t st);
+cudaError_t join_summary_init(const DevJob& j, cudaStream_t st);
+cudaError_t join_scan(const DevJob& j, cudaStream_t st);
 
 // per-unit launchers of the templated chain kernels (mc_inst_*.cu)
 #define MC_CHAIN_UNIT(name)                                                                              \

@@ -180,6 +180,8 @@ __global__ void clear_stats_kernel(const DevJob j) {
     j.stats[kStatQueuePrefix] = 0;
     j.stats[kStatPartial] = 0;
     j.stats[kStatWholeFill] = 0;
+    j.stats[kStatScanned] = 0;
+    j.stats[kStatFirstPending] = j.p;
   }
   // first accepted sample per segment: -1 = not searched yet
   const long long n = static_cast<long long>(j.p) * j.kcap;
@@ -195,9 +197,12 @@ __global__ void clear_stats_kernel(const DevJob j) {
 // their joint thresholds are rebuilt by tj_list_kernel.
 __global__ void __launch_bounds__(1024) mark_kernel(const DevJob j) {
   __shared__ int s_tmp[1024];
-  __shared__ int s_count;
+  __shared__ int s_count, s_first;
   block_last_accepted(j, s_tmp, j.lastacc);
-  if (threadIdx.x == 0) s_count = 0;
+  if (threadIdx.x == 0) {
+    s_count = 0;
+    s_first = j.p;
+  }
   __syncthreads();
   const int carry_in = j.stats[kStatCarryValid] ? static_cast<int>(j.stats[kStatCarry]) : -1;
   for (int i = threadIdx.x; i < j.p; i += blockDim.x) {
@@ -208,15 +213,131 @@ __global__ void __launch_bounds__(1024) mark_kernel(const DevJob j) {
       j.k[i] = -1;
       for (int s2 = 0; s2 < j.ck_K; ++s2) j.first[static_cast<size_t>(i) * j.kcap + s2] = -1;
       j.work[atomicAdd(&s_count, 1)] = i;
+      atomicMin(&s_first, i);
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     j.stats[kStatPending] = s_count;
+    j.stats[kStatFirstPending] = s_first;
     if (s_count) {
       j.stats[kStatPasses] += 1;
       j.stats[kStatMismatch] += s_count;
     }
+  }
+}
+
+// Summary replay, set-up: for the chains from the first pending one on, the
+// per-level minimum of the joint uniforms (kept in tj, whose rows are
+// rebuilt afterwards for the chains that still need a search) starts empty.
+__global__ void summary_init_kernel(const DevJob j) {
+  if (j.stats[kStatPending] == 0) return;
+  const int f = static_cast<int>(j.stats[kStatFirstPending]);
+  const long long n = static_cast<long long>(j.p - f) * j.np1;
+  uint32_t* base = j.tj + static_cast<size_t>(f) * j.np1;
+  for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < n;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x)
+    base[idx] = 0xFFFFFFFFu;
+  for (int i = f + blockIdx.x * blockDim.x + threadIdx.x; i < j.p; i += gridDim.x * blockDim.x) {
+    j.summ[i] = 0x7FFFFFFF;     // lowest level visited
+    j.summ[j.p + i] = -1;       // highest level visited
+    j.summ[2 * j.p + i] = 0;    // a level's minimum was 0xFFFFFFFF
+  }
+}
+
+// Exact resolution of the joint (Sec. 2 step 4) in chain order, from the
+// first chain whose speculated input was wrong: the input x of chain i is
+// the last level of the nearest earlier chain that kept samples (else the
+// carry).  Chain i keeps samples for input x iff some sample k passes
+// u_k <= thr(W[m_k] - W[x]), i.e. iff some visited level m has
+// min{u_k : m_k = m} <= thr(W[m] - W[x]) -- exact, from the summary replay.
+// Where x is the input k_i was already found for, k_i decides.  Chains that
+// keep samples under a new input are listed for one search pass (their x is
+// now exact, so nothing cascades); the others get k_i = 0.  A chain whose
+// answer the summary cannot give (a level whose every uniform was
+// 0xFFFFFFFF, against a threshold of 0xFFFFFFFF) stops the scan; the chains
+// from it on keep their speculated inputs for the ordinary passes.
+__global__ void __launch_bounds__(1024) scan_kernel(const DevJob j) {
+  if (j.stats[kStatPending] == 0) return;
+  constexpr int kChunk = 1024;
+  __shared__ int s_xu[kChunk], s_m[kChunk], s_lo[kChunk], s_hi[kChunk];
+  __shared__ signed char s_ks[kChunk], s_fl[kChunk];
+  __shared__ int s_count;
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int f = static_cast<int>(j.stats[kStatFirstPending]);
+  const int carry_in = j.stats[kStatCarryValid] ? static_cast<int>(j.stats[kStatCarry]) : -1;
+  int x = (j.lastacc[f] >= 0) ? j.m[j.lastacc[f]] : carry_in;
+  if (t == 0) s_count = 0;
+  int i = f, scanned = 0;
+  bool stopped = false;
+  for (int c0 = f; c0 < j.p && !stopped; c0 += kChunk) {
+    const int n = min(kChunk, j.p - c0);
+    __syncthreads();
+    for (int q = t; q < n; q += nt) {
+      const int c = c0 + q;
+      const int64_t kc = j.k[c];
+      s_xu[q] = j.xused[c];
+      s_ks[q] = kc > 0 ? 1 : (kc == 0 ? 0 : -1);
+      s_m[q] = j.m[c];
+      s_lo[q] = j.summ[c];
+      s_hi[q] = j.summ[j.p + c];
+      s_fl[q] = j.summ[2 * j.p + c] ? 1 : 0;
+    }
+    __syncthreads();
+    for (int q = 0; q < n; ++q) {
+      i = c0 + q;
+      const bool known = (x == s_xu[q] && s_ks[q] >= 0);
+      bool acc;
+      if (known) {
+        acc = s_ks[q] > 0;
+      } else if (x < 0) {
+        acc = true;  // no input yet: the chain is kept whole (k = 1)
+      } else {
+        const uint32_t* um = j.tj + static_cast<size_t>(i) * j.np1;
+        const double wx = j.W[x];
+        const bool flag = s_fl[q] != 0;
+        int hit = 0, amb = 0;
+        for (int m = s_lo[q] + t; m <= s_hi[q]; m += nt) {
+          const uint32_t u = um[m];
+          if (u != 0xFFFFFFFFu || flag) {
+            const uint32_t thr = threshold_det(__dsub_rn(j.W[m], wx));
+            if (u != 0xFFFFFFFFu) hit |= (u <= thr) ? 1 : 0;
+            else amb |= (thr == 0xFFFFFFFFu) ? 1 : 0;
+          }
+        }
+        acc = __syncthreads_or(hit) != 0;
+        if (!acc && __syncthreads_or(amb)) {
+          stopped = true;
+          break;
+        }
+        ++scanned;
+      }
+      if (!known) {
+        if (t == 0) {
+          j.xused[i] = x;
+          if (x < 0) {
+            j.k[i] = 1;
+          } else if (acc) {
+            j.k[i] = -1;
+            j.work[s_count++] = i;
+          } else {
+            j.k[i] = 0;
+          }
+        }
+        if (acc && x >= 0)
+          for (int s2 = t; s2 < j.ck_K; s2 += nt) j.first[static_cast<size_t>(i) * j.kcap + s2] = -1;
+      }
+      if (acc) x = s_m[q];
+    }
+    if (!stopped) i = c0 + n;
+  }
+  __syncthreads();
+  // stopped early: chains still waiting for a search keep their inputs
+  if (t == 0) {
+    for (int q = i; q < j.p; ++q)
+      if (j.k[q] < 0) j.work[s_count++] = q;
+    j.stats[kStatPending] = s_count;
+    j.stats[kStatScanned] = scanned;
   }
 }
 
@@ -338,6 +459,18 @@ __global__ void reset_queue_kernel(const DevJob j) {
   if (threadIdx.x == 0) j.stats[kStatQueueSearch] = 0;
 }
 
+cudaError_t join_summary_init(const DevJob& j, cudaStream_t st) {
+  summary_init_kernel<<<1024, 256, 0, st>>>(j);
+  launches_add(1);
+  return cudaGetLastError();
+}
+
+cudaError_t join_scan(const DevJob& j, cudaStream_t st) {
+  scan_kernel<<<1, 1024, 0, st>>>(j);
+  launches_add(1);
+  return cudaGetLastError();
+}
+
 cudaError_t join_reset_queue(const DevJob& j, cudaStream_t st) {
   reset_queue_kernel<<<1, 32, 0, st>>>(j);
   launches_add(1);
@@ -358,10 +491,15 @@ cudaError_t join_select(const DevJob& j, bool listed, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t join_mark(const DevJob& j, cudaStream_t st) {
+cudaError_t join_mark(const DevJob& j, cudaStream_t st, bool thresholds) {
   mark_kernel<<<1, 1024, 0, st>>>(j);
+  launches_add(1);
+  return thresholds ? join_tj_list(j, st) : cudaGetLastError();
+}
+
+cudaError_t join_tj_list(const DevJob& j, cudaStream_t st) {
   tj_list_kernel<<<256, 256, 0, st>>>(j);
-  launches_add(2);
+  launches_add(1);
   return cudaGetLastError();
 }
 

@@ -65,3 +65,29 @@ def canonical_weights(L: int, beta: float) -> np.ndarray:
     N = L * L
     E = -2 * N + 4 * np.arange(N + 1)
     return -beta * E.astype(np.float64)
+
+
+@dataclass(frozen=True)
+class ServedJob:
+    arrival: float   # seconds after the stream starts
+    L: int
+    chains: int
+    iterations: int
+    sweeps: int
+    seed: int
+
+
+SERVING_SIZES = (16, 32, 48, 64, 96, 128)
+
+
+def serving_stream(n_jobs: int, rate: float = 20.0, sweeps: int = 20, seed: int = 5) -> list[ServedJob]:
+    """Poisson arrivals (mean `rate` jobs/s) of weight-estimation jobs: L
+    uniform over SERVING_SIZES, chains uniform over 256, 512, ..., 4096,
+    weight iterations uniform over 20..60, `sweeps` sweeps per iteration,
+    job seed 1000 + index."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n_jobs))
+    Ls = rng.choice(np.array(SERVING_SIZES), n_jobs)
+    ps = 256 * rng.integers(1, 17, n_jobs)
+    its = rng.integers(20, 61, n_jobs)
+    return [ServedJob(float(t[i]), int(Ls[i]), int(ps[i]), int(its[i]), sweeps, 1000 + i) for i in range(n_jobs)]

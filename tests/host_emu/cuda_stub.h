@@ -25,3 +25,6 @@ inline long long __double_as_longlong(double d) { long long v; memcpy(&v, &d, 8)
 template <class T, class U> inline T atomicAdd(T* p, U v) { T o = *p; *p = o + (T)v; return o; }
 inline size_t __cvta_generic_to_shared(const void* p) { return (size_t)p; }
 template <class T> inline T __ldg(const T* p) { return *p; }
+template <class T> inline T atomicMin(T* p, T v) { T o = *p; if (v < o) *p = v; return o; }
+template <class T> inline T min(T a, T b) { return b < a ? b : a; }
+template <class T> inline T max(T a, T b) { return a < b ? b : a; }

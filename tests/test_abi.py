@@ -56,3 +56,11 @@ def test_init_rejects_bad_arguments(libpath):
         with pytest.raises(mc.McError) as e:
             mc.mc_init(L, p, 1, start)
         assert e.value.code == mc.MC_EINVAL
+
+
+def test_job_device_bytes_is_a_host_query(libpath):
+    assert mc.mc_job_device_bytes(6, 10, 1) == 0 and mc.mc_job_device_bytes(8, 0, 1) == 0
+    a = mc.mc_job_device_bytes(32, 100, 10)
+    assert a > 0
+    assert mc.mc_job_device_bytes(32, 200, 10) > a      # more chains, more memory
+    assert mc.mc_job_device_bytes(64, 100, 10) > a      # larger lattice, more memory
