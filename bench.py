@@ -482,7 +482,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--jobs", type=int, default=400, help="serving: jobs in the arrival stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
-    ap.add_argument("--slots", type=int, default=32, help="serving: server slots")
+    ap.add_argument("--slots", type=int, default=64, help="serving: server slots")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

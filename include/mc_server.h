@@ -9,7 +9,10 @@
  * stay resident on the device until it finishes.  Every slot has its own
  * CUDA stream, so the work of admitted jobs overlaps on the device; a host
  * thread of the server keeps each slot at most two iterations ahead of the
- * GPU and admits new jobs as slots and memory free up.  The dynamics of a
+ * GPU and admits new jobs as slots and memory free up.  Each job runs with
+ * its chains packed into as few warps as possible (a round takes as long
+ * as with the chains spread out, since one chain's latency sets it), so
+ * that concurrent jobs share the SMs.  The dynamics of a
  * job do not depend on what else runs: its result is identical to the same
  * job run alone through mc.h.
  *

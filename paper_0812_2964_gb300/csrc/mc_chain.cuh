@@ -155,6 +155,7 @@ __device__ __forceinline__ void sweep_row(uint32_t (&cur)[WD], const uint32_t (&
       }
     }
     uint32_t F = 0u;  // flips of this word
+    hook.word(nb);    // per-word set-up of the hook (the joint's uniforms)
     uint32_t t0, t1;
     {
       // first site of the word: state before it is known, one load
@@ -201,7 +202,7 @@ __device__ __forceinline__ void sweep_row(uint32_t (&cur)[WD], const uint32_t (&
         m4 += static_cast<int>(acc) * dl;
         f = acc;
         if (w == 0 && b == 0) f0 = acc;
-        hook.sample(m4);
+        hook.sample(m4, b);
       }
     }
     cur[w] ^= F;
@@ -210,15 +211,38 @@ __device__ __forceinline__ void sweep_row(uint32_t (&cur)[WD], const uint32_t (&
 }
 
 // ------------------------------------------------------------------ hooks
+// A hook sees every sample: word(nb) before the nb sites of each lattice
+// word, then sample(m4, b) after the attempt at site b of the word, with the
+// sample's level as m4 = 4 m (a byte offset into u32 arrays); b is a
+// compile-time constant once the site loop is unrolled.
+//
 // Generation: every sample adds 1 to its level's u32 counter in the block's
-// shared-memory histogram (one reduction, no branch).  Hooks receive the
-// level of the sample as m4 = 4 m (a byte offset into u32 arrays).
+// shared-memory histogram (one reduction, no branch).
 struct GenHook {
   uint32_t* hist;
   uint32_t run;  // unused; kept for a uniform hook interface
-  __device__ __forceinline__ void sample(int m4) { red_shared_add(hist, m4, 1u); }
+  __device__ __forceinline__ void word(int) {}
+  __device__ __forceinline__ void sample(int m4, int) { red_shared_add(hist, m4, 1u); }
   __device__ __forceinline__ void flush(int) {}
 };
+
+// Joint uniforms of the next nb samples k+1..k+nb (k a multiple of 4, as
+// every lattice word starts on a Philox block): Philox((k'-1)>>2, r, chain,
+// 1) word (k'-1)&3 for sample k'.
+__device__ __forceinline__ void joint_fill(uint32_t (&U)[32], const int nb, const int64_t k, const uint32_t r,
+                                           const uint32_t chain, const uint32_t k0, const uint32_t k1) {
+  const uint32_t blk = static_cast<uint32_t>(static_cast<uint64_t>(k) >> 2);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (4 * q < nb) {
+      const uint4 v = philox4x32_10(make_uint4(blk + static_cast<uint32_t>(q), r, chain, kTagJoint), k0, k1);
+      U[4 * q + 0] = v.x;
+      U[4 * q + 1] = v.y;
+      U[4 * q + 2] = v.z;
+      U[4 * q + 3] = v.w;
+    }
+  }
+}
 
 // Joint search (Sec. 2 step 4): for samples k = 1..M of the chain (the
 // configuration after attempt k of the round) draw the joint uniform
@@ -231,16 +255,12 @@ struct SearchHook {
   const uint32_t* __restrict__ tj;  // thresholds for moves x -> m, indexed by m
   int64_t k, M, found;
   uint32_t chain, r, k0, k1;
-  uint4 jr;
+  uint32_t uj[32];
   bool done;
-  __device__ __forceinline__ void sample(int m4) {
-    const int m = m4 >> 2;
+  __device__ __forceinline__ void word(int nb) { joint_fill(uj, nb, k, r, chain, k0, k1); }
+  __device__ __forceinline__ void sample(int m4, int b) {
     ++k;
-    const uint64_t q = static_cast<uint64_t>(k - 1);
-    if ((q & 3u) == 0u)
-      jr = philox4x32_10(make_uint4(static_cast<uint32_t>(q >> 2), r, chain, kTagJoint), k0, k1);
-    const uint32_t u = uint4_word(jr, static_cast<uint32_t>(q & 3u));
-    const bool hit = (u <= __ldg(&tj[m])) && !done && k <= M;
+    const bool hit = (uj[b] <= __ldg(&tj[m4 >> 2])) && !done && k <= M;
     found = hit ? k : found;
     done = done || hit;
   }
@@ -254,18 +274,16 @@ struct SummaryHook {
   uint32_t* umin;  // row of the chain, indexed by level
   int64_t k;
   uint32_t chain, r, k0, k1;
-  uint4 jr;
+  uint32_t uj[32];
   int cur, lo, hi;
   uint32_t run_min;
   bool flag;
   bool done;       // never set: the whole segment is summarised
-  __device__ __forceinline__ void sample(int m4) {
+  __device__ __forceinline__ void word(int nb) { joint_fill(uj, nb, k, r, chain, k0, k1); }
+  __device__ __forceinline__ void sample(int m4, int b) {
     const int m = m4 >> 2;
     ++k;
-    const uint64_t q = static_cast<uint64_t>(k - 1);
-    if ((q & 3u) == 0u)
-      jr = philox4x32_10(make_uint4(static_cast<uint32_t>(q >> 2), r, chain, kTagJoint), k0, k1);
-    const uint32_t u = uint4_word(jr, static_cast<uint32_t>(q & 3u));
+    const uint32_t u = uj[b];
     if (m != cur) {
       flush();
       cur = m;

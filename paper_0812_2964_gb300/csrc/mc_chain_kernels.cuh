@@ -317,7 +317,6 @@ __global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int c
           hk.r = r;
           hk.k0 = j.key0;
           hk.k1 = j.key1;
-          hk.jr = make_uint4(0u, 0u, 0u, 0u);
           hk.done = false;
           const int64_t k_begin = hk.k;
           replay_segment<Factory>(j, b, i, seg, t0, S, hk);
@@ -365,7 +364,6 @@ __global__ void __launch_bounds__(128) summary_kernel(const DevJob j, const int 
       hk.r = r;
       hk.k0 = j.key0;
       hk.k1 = j.key1;
-      hk.jr = make_uint4(0u, 0u, 0u, 0u);
       hk.cur = -1;
       hk.lo = 0x7FFFFFFF;
       hk.hi = -1;
@@ -390,7 +388,8 @@ struct PrefixHook {
   uint32_t* hist;
   int64_t k, cut;  // samples with index < cut are counted
   bool done;
-  __device__ __forceinline__ void sample(int m4) {
+  __device__ __forceinline__ void word(int) {}
+  __device__ __forceinline__ void sample(int m4, int) {
     if (done) return;
     ++k;
     if (k >= cut) {
@@ -547,7 +546,6 @@ __global__ void __launch_bounds__(128) resolve_kernel(const DevJob j, const int 
         hk.r = r;
         hk.k0 = j.key0;
         hk.k1 = j.key1;
-        hk.jr = make_uint4(0u, 0u, 0u, 0u);
         hk.done = false;
         replay_chain<Factory>(j, b, i, t0, S, hk);
         j.k[i] = hk.found;

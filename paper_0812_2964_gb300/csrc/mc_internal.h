@@ -117,6 +117,8 @@ MC_CHAIN_UNIT(chain_kernels_smem_L128);
 
 // launch shape chosen by default for (L, p)
 LaunchShape default_shape(int L, int p, int num_sms);
+// fullest warps with the same table placement (what concurrent jobs want)
+LaunchShape dense_shape(int L, int p, int num_sms);
 bool shape_supported(int L, const LaunchShape& s);
 size_t gen_smem_bytes(int L, const LaunchShape& s, bool* table_in_smem);
 

@@ -377,6 +377,24 @@ LaunchShape default_shape(int L, int p, int num_sms) {
   return s;
 }
 
+// Densest shape for L and p: as many chains per warp as there are (up to 32),
+// keeping the threshold table in shared memory if the default shape has it
+// there.  The time of a round is set by the latency of one chain, which a
+// fuller warp does not change (measured: within 5 % for L <= 64 and 128), so
+// a job shaped this way takes the same time on far fewer warps -- the rest
+// of the GPU stays free for other jobs (the server uses it).
+LaunchShape dense_shape(int L, int p, int num_sms) {
+  const LaunchShape def = default_shape(L, p, num_sms);
+  const bool ts = table_fits(L, def, true);
+  for (int cpw = std::min(32, std::max(1, p)); cpw >= 1; --cpw)
+    for (int w = 4; w >= 1; --w) {
+      LaunchShape s{def.placement, cpw, w};
+      if (w > 1 && (w - 1) * cpw >= p) continue;  // no empty warps
+      if (shape_supported(L, s) && (!ts || table_fits(L, s, true))) return s;
+    }
+  return def;
+}
+
 // The joint's replay kernels use full warps whatever shape generation runs
 // with (their work items are (chain, segment) pairs, not chains): 32 items a
 // warp, as many warps a block as fit, preferring a shape whose threshold

@@ -60,7 +60,7 @@ struct mc_server {
   int active = 0, peak_active = 0, finished = 0;
   uint64_t next_id = 1, admitted = 0, completed = 0;
   bool stopping = false;
-  int device = 0;
+  int device = 0, num_sms = 0;
   std::chrono::steady_clock::time_point t0;
   std::thread worker;
 
@@ -97,6 +97,11 @@ int admit_job(mc_server* srv, Rec* r) {
   mc_job* j = nullptr;
   int rc = mc_init(s.L, s.n_chains, s.seed, s.start, &j);
   if (rc == MC_OK) rc = mc_set_stream(j, srv->slots[r->slot].st);
+  if (rc == MC_OK) {
+    // fullest warps: the job's rounds take as long as alone, on fewer warps
+    const mcgpu::LaunchShape d = mcgpu::dense_shape(s.L, s.n_chains, srv->num_sms);
+    rc = mc_set_launch_shape(j, d.placement, d.cpw, d.wpb);
+  }
   if (rc != MC_OK) {
     r->err = mc_last_error();
     if (j) mc_free(j);
@@ -240,6 +245,7 @@ int mc_server_create(uint64_t budget_bytes, int max_slots, mc_server** out) {
   srv->budget = budget_bytes;
   srv->t0 = std::chrono::steady_clock::now();
   cudaError_t e = cudaGetDevice(&srv->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&srv->num_sms, cudaDevAttrMultiProcessorCount, srv->device);
   srv->slots.resize(max_slots);
   for (auto& sl : srv->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
