@@ -189,6 +189,7 @@ int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
       (rc = dalloc(j, &d.k, n_chains)) ||
       (rc = dalloc(j, &d.xused, n_chains)) || (rc = dalloc(j, &d.tj, static_cast<size_t>(n_chains) * np1)) ||
       (rc = dalloc(j, &d.offsets, n_chains)) || (rc = dalloc(j, &d.work, n_chains)) ||
+      (rc = dalloc(j, &d.work2, n_chains)) ||
       (rc = dalloc(j, &d.lastacc, n_chains)) || (rc = dalloc(j, &d.summ, 3ull * n_chains)) ||
       (rc = dalloc(j, &d.stats, mcgpu::kStatCount))) {
     free_all(j);
@@ -739,9 +740,9 @@ uint64_t mc_job_device_bytes(int L, int n_chains, int64_t sweeps) {
   const uint64_t N = static_cast<uint64_t>(L) * L, np1 = N + 1, wd = (L + 31) / 32;
   const uint64_t p = static_cast<uint64_t>(n_chains), lw = static_cast<uint64_t>(L) * wd, lat = p * lw;
   // as allocated by mc_init: spins, spins0, m, m0, W, T, h, hgen, dpre, k,
-  // xused, tj, offsets, work, lastacc, summ, stats
+  // xused, tj, offsets, work, work2, lastacc, summ, stats
   uint64_t b = lat * 4 * 2 + p * 4 * 2 + np1 * 8 + 5 * np1 * 4 + np1 * 8 * 3 + p * 8 + p * 4 + p * np1 * 4 +
-               p * 8 + p * 4 + p * 4 + p * 12 + mcgpu::kStatCount * 8;
+               p * 8 + p * 4 + p * 4 + p * 4 + p * 12 + mcgpu::kStatCount * 8;
   int K = 0, C = 0;
   round_segments(L * L, sweeps, &K, &C);
   return b + static_cast<uint64_t>(K) * p * (lw * 4 + 4 + 8 + 8);

@@ -269,25 +269,34 @@ __device__ __forceinline__ void replay_segment(const DevJob& j, const BlockCtx& 
     run.template sweep<true>(m, pf, b.T, j.np1, static_cast<uint32_t>(i), j.key0, j.key1, hk);
 }
 
-// Joint search (step 4) on all segments at once: work item (chain, segment)
-// finds the first sample inside the segment that passes the Metropolis test
-// against the chain's input level (0 if none).  Persistent: each warp takes
-// the next cpw consecutive items (segment-major: one segment of consecutive
+// Joint search (step 4) over segments [seg_lo, seg_hi): work item (chain,
+// segment) finds the first sample inside the segment that passes the
+// Metropolis test against the chain's input level (0 if none).  The chains
+// are all of them (list_mode 0), work[] (1, a resolution pass) or work2[]
+// (2, those without a hit in segment 0).  Persistent: each warp takes the
+// next cpw consecutive items (segment-major: one segment of consecutive
 // chains) from a global counter, its lanes replay them side by side, and
 // only then takes more, so a long replay holds up one warp, not a wave of
 // blocks.  A segment is skipped when an earlier segment of its chain has
-// already found an accepted sample (first[] is -1 until written).  Listed
-// chains only (resolution passes) when use_list is set.
+// already found an accepted sample (first[] is -1 until written).  A block
+// that starts after the queue ran dry leaves before any set-up.
 template <class Factory, bool TSMEM>
 __global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int cpw, const uint64_t t0,
-                                                     const int64_t S, const uint32_t r, const int use_list) {
-  const int nchains = use_list ? static_cast<int>(j.stats[kStatPending]) : j.p;
-  const long long items = static_cast<long long>(nchains) * j.ck_K;
+                                                     const int64_t S, const uint32_t r, const int list_mode,
+                                                     const int seg_lo, const int seg_hi_in) {
+  const int nchains = list_mode == 0 ? j.p : static_cast<int>(j.stats[list_mode == 1 ? kStatPending : kStatNoHit]);
+  const int seg_hi = min(seg_hi_in, j.ck_K);
+  const long long items = static_cast<long long>(nchains) * max(0, seg_hi - seg_lo);
   if (items == 0) return;
+  unsigned long long* queue = reinterpret_cast<unsigned long long*>(&j.stats[kStatQueueSearch]);
+  __shared__ int s_dry;
+  if (threadIdx.x == 0) s_dry = static_cast<long long>(__ldcg(reinterpret_cast<const long long*>(queue))) >= items;
+  __syncthreads();
+  if (s_dry) return;
+  const int32_t* list = list_mode == 1 ? j.work : j.work2;
   const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, false);
   BlockCtx b = block_setup<TSMEM>(j, sp, cpw, 0, false);
   __syncthreads();
-  unsigned long long* queue = reinterpret_cast<unsigned long long*>(&j.stats[kStatQueueSearch]);
   long long searched = 0;
   for (;;) {
     long long base = 0;
@@ -296,9 +305,9 @@ __global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int c
     if (base >= items) break;
     const long long item = base + b.lane;
     if (b.lane < cpw && item < items) {
-      const int seg = static_cast<int>(item / nchains);
+      const int seg = seg_lo + static_cast<int>(item / nchains);
       const int q = static_cast<int>(item % nchains);
-      const int i = use_list ? j.work[q] : q;
+      const int i = list_mode ? list[q] : q;
       int64_t* fi = j.first + static_cast<size_t>(i) * j.kcap;
       bool earlier = false;
       for (int s2 = 0; s2 < seg && !earlier; ++s2) earlier = __ldcg(&fi[s2]) > 0;
@@ -639,27 +648,39 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
   // persistent grids: the blocks that are resident at once, no more than needed
   const unsigned grid_all = static_cast<unsigned>(
       std::min<long long>(blocks_for(items, per_block), resident_blocks(kq, 32 * s.wpb, bytes)));
-  // speculated inputs: every chain, every segment
-  if ((e = join_reset_queue(j, st)) != cudaSuccess) return e;
-  kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, 0);
+  // a search over the chains of list_mode: their first segments, then the
+  // later segments of those without a hit there
+  auto search = [&](int list_mode) -> cudaError_t {
+    cudaError_t e2 = join_reset_queue(j, st);
+    if (e2 != cudaSuccess) return e2;
+    kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, list_mode, 0, 1);
+    launches_add(1);
+    if (j.ck_K > 1) {
+      if ((e2 = join_nohit(j, list_mode, st)) != cudaSuccess) return e2;
+      if ((e2 = join_reset_queue(j, st)) != cudaSuccess) return e2;
+      kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, 2, 1, j.ck_K);
+      launches_add(1);
+    }
+    return cudaGetLastError();
+  };
+  // speculated inputs: every chain
+  if ((e = search(0)) != cudaSuccess) return e;
   if ((e = join_select(j, false, st)) != cudaSuccess) return e;
   // grid-wide speculative resolution passes
   auto pass = [&](int n) -> cudaError_t {
     for (int q = 0; q < n; ++q) {
       cudaError_t e2 = join_mark(j, st);
-      if (e2 == cudaSuccess) e2 = join_reset_queue(j, st);
+      if (e2 == cudaSuccess) e2 = search(1);
+      if (e2 == cudaSuccess) e2 = join_select(j, true, st);
       if (e2 != cudaSuccess) return e2;
-      kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, 1);
-      launches_add(1);
-      if ((e2 = join_select(j, true, st)) != cudaSuccess) return e2;
     }
     return cudaSuccess;
   };
   const bool exact_scan = static_cast<long long>(j.p) * S * j.N <= kScanMaxSamples;
   if (exact_scan) {
     // a few speculative passes; if chains are still pending, the summary
-    // replay and the exact scan settle every input, one search pass finds
-    // the new k's, and the ordinary passes catch what the scan left
+    // replay and the exact scan settle every input, one search finds the
+    // new k's, and the ordinary passes catch what the scan left
     if ((e = pass(kGridPassesScan)) != cudaSuccess) return e;
     if ((e = join_mark(j, st, false)) != cudaSuccess) return e;
     if ((e = join_summary_init(j, st)) != cudaSuccess) return e;
@@ -674,15 +695,12 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
     launches_add(1);
     if ((e = join_scan(j, st)) != cudaSuccess) return e;
     if ((e = join_tj_list(j, st)) != cudaSuccess) return e;
-    if ((e = join_reset_queue(j, st)) != cudaSuccess) return e;
-    kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, 1);
-    launches_add(1);
+    if ((e = search(1)) != cudaSuccess) return e;
     if ((e = join_select(j, true, st)) != cudaSuccess) return e;
     if ((e = pass(kGridPassesScan)) != cudaSuccess) return e;
   } else {
     if ((e = pass(kGridPasses)) != cudaSuccess) return e;
   }
-  launches_add(1);
   auto kr = resolve_kernel<F, TS>;
   if ((e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=
       cudaSuccess)

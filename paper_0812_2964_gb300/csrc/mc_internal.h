@@ -37,6 +37,7 @@ struct DevJob {
   uint32_t* tj;        // [p][np1] joint thresholds for each chain's input
   int64_t* offsets;    // [p] position of each kept segment in the joined chain
   int32_t* work;       // [p] scratch list of chains
+  int32_t* work2;      // [p] chains without a hit in their first segment
   int32_t* lastacc;    // [p] last chain before i that kept samples (-1: none)
   int32_t* trace;      // [S][p] energy after each sweep (nullable)
   uint32_t* ckpt;      // [kcap][L*wd][p] lattice at the start of each round segment
@@ -66,7 +67,8 @@ enum StatIndex : int {
   kStatPartial = 12,     // partial-segment items of the prefix pass (listed after the whole ones)
   kStatFirstPending = 13,// lowest chain queued by the last mark pass (p if none)
   kStatScanned = 14,     // chains whose input the exact scan settled (last joint)
-  kStatCount = 15
+  kStatNoHit = 15,       // chains listed in work2
+  kStatCount = 16
 };
 
 // ---- kernels (mc_kernels.cu) ----
@@ -90,6 +92,8 @@ constexpr long long kScanMaxSamples = 20000000000ll;
 cudaError_t join_prelude(const DevJob& j, cudaStream_t st);
 cudaError_t join_mark(const DevJob& j, cudaStream_t st, bool thresholds = true);
 cudaError_t join_tj_list(const DevJob& j, cudaStream_t st);
+// list (in work2) the chains of list_mode (0 all, 1 work) with no hit in segment 0
+cudaError_t join_nohit(const DevJob& j, int list_mode, cudaStream_t st);
 cudaError_t join_select(const DevJob& j, bool listed, cudaStream_t st);
 cudaError_t join_prefix_list(const DevJob& j, cudaStream_t st);
 cudaError_t join_reset_queue(const DevJob& j, cudaStream_t st);

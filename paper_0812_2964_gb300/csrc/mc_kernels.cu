@@ -351,6 +351,22 @@ __global__ void tj_list_kernel(const DevJob j) {
   }
 }
 
+// Chains of the list (all, or work[]) that found no accepted sample in
+// their first segment go to work2 -- only they need their later segments
+// searched (one block).
+__global__ void __launch_bounds__(1024) nohit_kernel(const DevJob j, const int list_mode) {
+  __shared__ int s_count;
+  if (threadIdx.x == 0) s_count = 0;
+  __syncthreads();
+  const int n = list_mode ? static_cast<int>(j.stats[kStatPending]) : j.p;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int i = list_mode ? j.work[q] : q;
+    if (j.first[static_cast<size_t>(i) * j.kcap] == 0) j.work2[atomicAdd(&s_count, 1)] = i;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) j.stats[kStatNoHit] = s_count;
+}
+
 // ------------------------------------------------------------------ host side
 size_t gen_smem_bytes(int L, const LaunchShape& s, bool* table_in_smem) {
   const bool ts = table_fits(L, s, true);
@@ -513,6 +529,12 @@ cudaError_t join_mark(const DevJob& j, cudaStream_t st, bool thresholds) {
   mark_kernel<<<1, 1024, 0, st>>>(j);
   launches_add(1);
   return thresholds ? join_tj_list(j, st) : cudaGetLastError();
+}
+
+cudaError_t join_nohit(const DevJob& j, int list_mode, cudaStream_t st) {
+  nohit_kernel<<<1, 1024, 0, st>>>(j, list_mode);
+  launches_add(1);
+  return cudaGetLastError();
 }
 
 cudaError_t join_tj_list(const DevJob& j, cudaStream_t st) {
