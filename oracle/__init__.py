@@ -57,6 +57,7 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _i8p = ctypes.POINTER(ctypes.c_int8)
 _dp = ctypes.POINTER(ctypes.c_double)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
 
 
 def _declare(L):
@@ -98,6 +99,8 @@ def _declare(L):
         "or_get_last_S": (c.c_int64, [c.c_void_p]),
         "or_get_samples": (None, [c.c_void_p, _i32p]),
         "or_set_samples": (c.c_int, [c.c_void_p, c.c_int64, _i32p]),
+        "or_get_visited": (None, [c.c_void_p, _u8p]),
+        "or_thermo": (None, [c.c_int, _dp, _u8p, _dp, c.c_int, _dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -187,6 +190,18 @@ def joint_scan(levels, W, x_level, seed, r, i):
     lv = np.ascontiguousarray(levels, dtype=np.int32)
     W = np.ascontiguousarray(W, dtype=np.float64)
     return int(lib().or_joint_scan(_p(lv, _i32p), lv.size, _p(W, _dp), int(x_level), seed, r, i))
+
+
+def thermo(L, W, visited, betas):
+    """E, C, F, S at each beta (columns), from ln-weights W over the visited
+    levels (Eq. reweighting2).  Returns an array [len(betas)][4]."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    v = np.ascontiguousarray(visited, dtype=np.uint8)
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    assert W.size == v.size == L * L + 1
+    out = np.zeros((b.size, 4), dtype=np.float64)
+    lib().or_thermo(L, _p(W, _dp), _p(v, _u8p), _p(b, _dp), b.size, _p(out, _dp))
+    return out
 
 
 # ---------------------------------------------------------------- a whole job
@@ -282,6 +297,12 @@ class Job:
     @property
     def t(self):
         return int(lib().or_get_t(self._h))
+
+    @property
+    def visited(self):
+        out = np.zeros(self.N + 1, dtype=np.uint8)
+        lib().or_get_visited(self._h, _p(out, _u8p))
+        return out
 
     @property
     def round(self):

@@ -336,6 +336,7 @@ struct or_job {
     int32_t *samples;   /* [p][M] levels of the last round's samples */
     int32_t *trace;     /* [p][S] level after each sweep */
     int64_t *k;         /* [p] first kept sample of the last joint (0 = none) */
+    uint8_t *visited;   /* [N+1] 1 once a weight update has seen h > 0 there */
 };
 
 or_job *or_create(int L, int p, uint64_t seed, int start)
@@ -352,6 +353,7 @@ or_job *or_create(int L, int p, uint64_t seed, int start)
     j->T = (uint32_t *)malloc(sizeof(uint32_t) * 5 * ((size_t)j->N + 1));
     j->h = (int64_t *)calloc((size_t)j->N + 1, sizeof(int64_t));     /* step 1: h(E) = 0 */
     j->k = (int64_t *)calloc((size_t)p, sizeof(int64_t));
+    j->visited = (uint8_t *)calloc((size_t)j->N + 1, 1);
     for (int c = 0; c < p; ++c) {
         int8_t *s = j->spins + (size_t)c * j->N;
         or_init_lattice(s, L, seed, (uint32_t)c, start);
@@ -365,7 +367,7 @@ void or_free(or_job *j)
 {
     if (!j) return;
     free(j->spins); free(j->m); free(j->W); free(j->T); free(j->h);
-    free(j->samples); free(j->trace); free(j->k);
+    free(j->samples); free(j->trace); free(j->k); free(j->visited);
     free(j);
 }
 
@@ -470,8 +472,10 @@ int64_t or_join_naive(or_job *j)
 void or_update_weights(or_job *j)
 {
     for (int m = 0; m <= j->N; ++m) {
-        if (j->h[m] > 0)
+        if (j->h[m] > 0) {
             j->W[m] = j->W[m] - or_log_det((double)j->h[m]);
+            j->visited[m] = 1;
+        }
         j->h[m] = 0;
     }
     or_build_table(j->W, j->L, j->T);
@@ -512,6 +516,7 @@ void or_get_trace(const or_job *j, int32_t *trace)
 void or_get_k(const or_job *j, int64_t *k) { memcpy(k, j->k, sizeof(int64_t) * (size_t)j->p); }
 int32_t or_get_carry(const or_job *j, int *valid) { if (valid) *valid = j->carry_valid; return j->carry; }
 uint64_t or_get_t(const or_job *j) { return j->t; }
+void or_get_visited(const or_job *j, uint8_t *v) { memcpy(v, j->visited, (size_t)j->N + 1); }
 uint32_t or_get_round(const or_job *j) { return j->r; }
 int64_t or_get_last_S(const or_job *j) { return j->last_S; }
 /* Test hook: install hand-made samples for the last round (S sweeps), so that
@@ -531,4 +536,63 @@ int or_set_samples(or_job *j, int64_t S, const int32_t *samples)
 void or_get_samples(const or_job *j, int32_t *samples)
 {
     memcpy(samples, j->samples, sizeof(int32_t) * (size_t)j->p * (size_t)(j->last_S * (int64_t)j->N));
+}
+
+/* ------------------------------------------------------------------ */
+/* Statistical averages at inverse temperature beta (Sec. 3.2, Eq.     */
+/* reweighting2; Sec. 4.1 for E, C, F, S).  With W = ln w and the       */
+/* density of states D(E) proportional to 1/w(E), over the levels the   */
+/* weight iteration has visited:                                        */
+/*   <O> = sum_E O(E) e^{-W(E) - beta E} / sum_E e^{-W(E) - beta E},     */
+/* every exponential taken relative to the largest exponent (the        */
+/* logarithmic evaluation Sec. 4.2 asks for).  E = <H>,                  */
+/* C = beta^2 (<H^2> - <H>^2) summed as beta^2 <(H - <H>)^2>.  D is      */
+/* normalised so that it counts all 2^N states:                          */
+/*   ln Z = N ln 2 + ln sum_E e^{-W - beta E} - ln sum_E e^{-W},         */
+/* F = -ln Z / beta, S = beta (E - F).                                   */
+/* out[4 b + 0..3] = E, C, F, S at betas[b].  Plain libm exp/log: these */
+/* averages are compared with a tolerance, not bit for bit.             */
+/* ------------------------------------------------------------------ */
+void or_thermo(int L, const double *W, const uint8_t *visited, const double *betas, int nb, double *out)
+{
+    const int N = L * L;
+    double bmax = -INFINITY;
+    for (int m = 0; m <= N; ++m)
+        if (visited[m] && -W[m] > bmax) bmax = -W[m];
+    double sg = 0.0;
+    for (int m = 0; m <= N; ++m)
+        if (visited[m]) sg += exp(-W[m] - bmax);
+    const double ln_norm = bmax + log(sg);           /* ln sum_E e^{-W} */
+    for (int b = 0; b < nb; ++b) {
+        const double beta = betas[b];
+        double amax = -INFINITY;
+        for (int m = 0; m <= N; ++m) {
+            if (!visited[m]) continue;
+            const double E = (double)(4 * m - 2 * N);
+            const double a = -W[m] - beta * E;
+            if (a > amax) amax = a;
+        }
+        double z = 0.0, e1 = 0.0;
+        for (int m = 0; m <= N; ++m) {
+            if (!visited[m]) continue;
+            const double E = (double)(4 * m - 2 * N);
+            const double wgt = exp(-W[m] - beta * E - amax);
+            z += wgt;
+            e1 += E * wgt;
+        }
+        const double Eav = e1 / z;
+        double v = 0.0;
+        for (int m = 0; m <= N; ++m) {
+            if (!visited[m]) continue;
+            const double E = (double)(4 * m - 2 * N);
+            const double wgt = exp(-W[m] - beta * E - amax);
+            v += (E - Eav) * (E - Eav) * wgt;
+        }
+        const double lnZ = (double)N * log(2.0) + amax + log(z) - ln_norm;
+        const double F = -lnZ / beta;
+        out[4 * b + 0] = Eav;
+        out[4 * b + 1] = beta * beta * (v / z);
+        out[4 * b + 2] = F;
+        out[4 * b + 3] = beta * (Eav - F);
+    }
 }

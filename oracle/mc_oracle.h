@@ -81,10 +81,15 @@ void    or_get_trace(const or_job *j, int32_t *trace);
 void    or_get_k(const or_job *j, int64_t *k);
 int32_t or_get_carry(const or_job *j, int *valid);
 uint64_t or_get_t(const or_job *j);
+void    or_get_visited(const or_job *j, uint8_t *visited);
 uint32_t or_get_round(const or_job *j);
 int64_t or_get_last_S(const or_job *j);
 void    or_get_samples(const or_job *j, int32_t *samples);
 int     or_set_samples(or_job *j, int64_t S, const int32_t *samples);
+
+/* ---- part (ii): statistical averages from a weight (Eq. reweighting2) ---- */
+/* out[4b..4b+3] = E, C, F, S at betas[b] over the levels with visited[m] */
+void or_thermo(int L, const double *W, const uint8_t *visited, const double *betas, int nb, double *out);
 
 #ifdef __cplusplus
 }
