@@ -124,6 +124,25 @@ int mc_update_weights(mc_job *job);
 int mc_get_weights(mc_job *job, double *out, int n);
 int mc_set_weights(mc_job *job, const double *w, int n);
 
+/* Levels the weight iteration has visited: out[m] = 1 once a weight update
+ * (mc_update_weights) saw h[m] > 0, else 0; n = N+1.  These are the
+ * energies the statistical averages sum over.  mc_set_visited restores a
+ * saved mask (nonzero = 1; MC_ESTATE while a round is pending).  Both
+ * synchronise. */
+int mc_get_visited(mc_job *job, uint8_t *out, int n);
+int mc_set_visited(mc_job *job, const uint8_t *in, int n);
+
+/* Part (ii) of the paper (Sec. 3.2, Eq. reweighting2; quantities of
+ * Sec. 4.1): statistical averages of the Ising model at inverse
+ * temperatures betas[0..n_beta-1] (each > 0, 1 <= n_beta <= 65535) from the
+ * job's current weight, with the density of states taken as
+ * D(E) ~ 1/w(E) = e^{-W(E)} over the visited levels and normalised to 2^N
+ * states: out[4b + 0..3] = E = <H>, C = beta^2 (<H^2> - <H>^2),
+ * F = -ln Z / beta, S = beta (E - F) (J = k_B = 1).  Evaluated in FP64
+ * relative to the largest exponent; deterministic.  Host arrays;
+ * synchronises. */
+int mc_thermo(mc_job *job, const double *betas, int n_beta, double *out);
+
 /* Acceptance thresholds, planar: out[a*(N+1) + m] for the move from level m
  * to m + a - 2 (a = number of aligned neighbours), n = 5*(N+1).  A uniform
  * u is accepted iff u <= threshold.  Synchronises. */

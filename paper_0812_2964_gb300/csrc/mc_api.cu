@@ -190,7 +190,7 @@ int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
       (rc = dalloc(j, &d.xused, n_chains)) || (rc = dalloc(j, &d.tj, static_cast<size_t>(n_chains) * np1)) ||
       (rc = dalloc(j, &d.offsets, n_chains)) || (rc = dalloc(j, &d.work, n_chains)) ||
       (rc = dalloc(j, &d.work2, n_chains)) ||
-      (rc = dalloc(j, &d.lastacc, n_chains)) || (rc = dalloc(j, &d.summ, 3ull * n_chains)) ||
+      (rc = dalloc(j, &d.lastacc, n_chains)) || (rc = dalloc(j, &d.summ, 3ull * n_chains)) || (rc = dalloc(j, &d.visited, np1)) ||
       (rc = dalloc(j, &d.stats, mcgpu::kStatCount))) {
     free_all(j);
     delete j;
@@ -199,6 +199,7 @@ int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
   cudaStream_t st = j->stream;
   e = cudaMemsetAsync(d.W, 0, sizeof(double) * np1, st);  // w^(1) = 1
   if (e == cudaSuccess) e = cudaMemsetAsync(d.h, 0, sizeof(long long) * np1, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.visited, 0, np1, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.hgen, 0, sizeof(unsigned long long) * np1, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.dpre, 0, sizeof(unsigned long long) * np1, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.stats, 0, sizeof(long long) * mcgpu::kStatCount, st);
@@ -538,6 +539,41 @@ int mc_set_weights(mc_job* job, const double* w, int n) {
   return sync(job, "set weights");
 }
 
+int mc_get_visited(mc_job* job, uint8_t* out, int n) {
+  if (int rc = check_job(job)) return rc;
+  if (!out || n != job->N + 1) return fail(MC_EINVAL, "visited mask needs N+1 = %d entries", job->N + 1);
+  MC_CUDA(cudaMemcpyAsync(out, job->d.visited, n, cudaMemcpyDeviceToHost, job->stream), "visited copy");
+  return sync(job, "visited");
+}
+
+int mc_set_visited(mc_job* job, const uint8_t* in, int n) {
+  if (int rc = check_job(job)) return rc;
+  if (job->pending) return fail(MC_ESTATE, "round pending");
+  if (!in || n != job->N + 1) return fail(MC_EINVAL, "visited mask needs N+1 = %d entries", job->N + 1);
+  std::vector<uint8_t> v(in, in + n);
+  for (auto& x : v) x = x ? 1 : 0;
+  MC_CUDA(cudaMemcpyAsync(job->d.visited, v.data(), n, cudaMemcpyHostToDevice, job->stream), "visited copy");
+  return sync(job, "visited");
+}
+
+int mc_thermo(mc_job* job, const double* betas, int n_beta, double* out) {
+  if (int rc = check_job(job)) return rc;
+  if (!betas || !out || n_beta < 1 || n_beta > 65535) return fail(MC_EINVAL, "need 1..65535 betas and an output");
+  for (int b = 0; b < n_beta; ++b)
+    if (!(betas[b] > 0.0) || !(betas[b] < 1e300)) return fail(MC_EINVAL, "beta[%d] must be positive and finite", b);
+  void* dev = nullptr;
+  MC_CUDA(raw_alloc(job, &dev, sizeof(double) * 5 * n_beta), "thermo buffer");
+  double* db = static_cast<double*>(dev);
+  double* dout = db + n_beta;
+  cudaError_t e = cudaMemcpyAsync(db, betas, sizeof(double) * n_beta, cudaMemcpyHostToDevice, job->stream);
+  if (e == cudaSuccess) e = mcgpu::k_thermo(job->d, db, n_beta, dout, job->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, dout, sizeof(double) * 4 * n_beta, cudaMemcpyDeviceToHost, job->stream);
+  raw_free(job, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "thermo");
+  return sync(job, "thermo");
+}
+
 int mc_get_table(mc_job* job, uint32_t* out, int n) {
   if (int rc = check_job(job)) return rc;
   if (!out || n != 5 * (job->N + 1)) return fail(MC_EINVAL, "table needs 5*(N+1) entries");
@@ -740,9 +776,9 @@ uint64_t mc_job_device_bytes(int L, int n_chains, int64_t sweeps) {
   const uint64_t N = static_cast<uint64_t>(L) * L, np1 = N + 1, wd = (L + 31) / 32;
   const uint64_t p = static_cast<uint64_t>(n_chains), lw = static_cast<uint64_t>(L) * wd, lat = p * lw;
   // as allocated by mc_init: spins, spins0, m, m0, W, T, h, hgen, dpre, k,
-  // xused, tj, offsets, work, work2, lastacc, summ, stats
+  // xused, tj, offsets, work, work2, lastacc, summ, visited, stats
   uint64_t b = lat * 4 * 2 + p * 4 * 2 + np1 * 8 + 5 * np1 * 4 + np1 * 8 * 3 + p * 8 + p * 4 + p * np1 * 4 +
-               p * 8 + p * 4 + p * 4 + p * 4 + p * 12 + mcgpu::kStatCount * 8;
+               p * 8 + p * 4 + p * 4 + p * 4 + p * 12 + np1 + mcgpu::kStatCount * 8;
   int K = 0, C = 0;
   round_segments(L * L, sweeps, &K, &C);
   return b + static_cast<uint64_t>(K) * p * (lw * 4 + 4 + 8 + 8);

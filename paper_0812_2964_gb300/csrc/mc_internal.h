@@ -45,6 +45,7 @@ struct DevJob {
   int64_t* first;      // [p][kcap] first accepted sample inside each segment (0: none)
   int2* plist;         // [p*kcap] (chain, segment) work list of the prefix pass
   int32_t* summ;       // [3][p] summary pass: lowest and highest level visited, flag
+  uint8_t* visited;    // [np1] 1 once a weight update has seen h > 0 at the level
   int ck_C;            // sweeps per segment in the current round
   int ck_K;            // segments in the current round
   int kcap;            // segment capacity
@@ -76,6 +77,8 @@ cudaError_t k_init_lattice(const DevJob& j, int start, cudaStream_t st);
 cudaError_t k_levels(const DevJob& j, cudaStream_t st);
 cudaError_t k_build_table(const DevJob& j, cudaStream_t st);
 cudaError_t k_update_weights(const DevJob& j, cudaStream_t st);
+// E, C, F, S at n inverse temperatures (device arrays betas[n], out[n][4])
+cudaError_t k_thermo(const DevJob& j, const double* betas, int n, double* out, cudaStream_t st);
 cudaError_t k_generate(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S,
                        bool trace, cudaStream_t st);
 cudaError_t k_join(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S, uint32_t r,

@@ -4,6 +4,7 @@
 // (Sec. 3.1 Eq. new_weight in logarithms, Sec. 4.2).
 #include <atomic>
 #include <algorithm>
+#include <math_constants.h>
 
 #include "mc_chain_kernels.cuh"
 
@@ -80,8 +81,94 @@ __global__ void weights_kernel(const DevJob j) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= j.np1) return;
   const long long h = j.h[m];
-  if (h > 0) j.W[m] = __dsub_rn(j.W[m], log_det(static_cast<double>(h)));
+  if (h > 0) {
+    j.W[m] = __dsub_rn(j.W[m], log_det(static_cast<double>(h)));
+    j.visited[m] = 1;
+  }
   j.h[m] = 0;
+}
+
+// ------------------------------------------------------------------ part (ii)
+// Statistical averages at inverse temperature beta (Sec. 3.2, Eq.
+// reweighting2, with E, C, F, S of Sec. 4.1), one block per beta.  D(E) is
+// proportional to 1/w(E) = e^{-W(E)} over the levels the weight iteration
+// has visited; every sum is taken relative to its largest exponent (the
+// logarithmic evaluation of Sec. 4.2).  D counts all 2^N states:
+// ln Z = N ln 2 + ln sum e^{-W - beta E} - ln sum e^{-W}.
+// C = beta^2 <(H - <H>)^2>, F = -ln Z / beta, S = beta (E - F).
+// Reductions are fixed-shape trees, so repeated calls agree bit for bit.
+constexpr int kThermoThreads = 256;
+
+__device__ double block_max(double v, double* sh) {
+  const int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int o = kThermoThreads / 2; o > 0; o >>= 1) {
+    if (t < o) sh[t] = fmax(sh[t], sh[t + o]);
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ double block_sum(double v, double* sh) {
+  const int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int o = kThermoThreads / 2; o > 0; o >>= 1) {
+    if (t < o) sh[t] = sh[t] + sh[t + o];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kThermoThreads) thermo_kernel(const DevJob j, const double* __restrict__ betas,
+                                                                double* __restrict__ out) {
+  __shared__ double sh[kThermoThreads];
+  const int t = threadIdx.x;
+  const double beta = betas[blockIdx.x];
+  double bm = -CUDART_INF, am = -CUDART_INF;
+  for (int m = t; m < j.np1; m += kThermoThreads)
+    if (j.visited[m]) {
+      const double E = static_cast<double>(4 * m - 2 * j.N);
+      bm = fmax(bm, -j.W[m]);
+      am = fmax(am, -j.W[m] - beta * E);
+    }
+  const double B = block_max(bm, sh);
+  const double A = block_max(am, sh);
+  double sg = 0.0, z = 0.0, e1 = 0.0;
+  for (int m = t; m < j.np1; m += kThermoThreads)
+    if (j.visited[m]) {
+      const double E = static_cast<double>(4 * m - 2 * j.N);
+      const double w = exp(-j.W[m] - beta * E - A);
+      sg += exp(-j.W[m] - B);
+      z += w;
+      e1 += E * w;
+    }
+  const double SG = block_sum(sg, sh);
+  const double Z = block_sum(z, sh);
+  const double E1 = block_sum(e1, sh);
+  const double Eav = E1 / Z;
+  double v = 0.0;
+  for (int m = t; m < j.np1; m += kThermoThreads)
+    if (j.visited[m]) {
+      const double E = static_cast<double>(4 * m - 2 * j.N);
+      const double w = exp(-j.W[m] - beta * E - A);
+      v += (E - Eav) * (E - Eav) * w;
+    }
+  const double V = block_sum(v, sh);
+  if (t == 0) {
+    const double lnZ = static_cast<double>(j.N) * log(2.0) + A + log(Z) - (B + log(SG));
+    const double F = -lnZ / beta;
+    double* o = out + 4 * blockIdx.x;
+    o[0] = Eav;
+    o[1] = beta * beta * (V / Z);
+    o[2] = F;
+    o[3] = beta * (Eav - F);
+  }
 }
 
 // Joint thresholds for each listed chain's input level x: tj[i][m] = thr(W[m] - W[x]).
@@ -603,6 +690,12 @@ cudaError_t k_levels(const DevJob& j, cudaStream_t st) {
 
 cudaError_t k_build_table(const DevJob& j, cudaStream_t st) {
   table_kernel<<<blocks_for(5ll * j.np1, 256), 256, 0, st>>>(j);
+  launches_add(1);
+  return cudaGetLastError();
+}
+
+cudaError_t k_thermo(const DevJob& j, const double* betas, int n, double* out, cudaStream_t st) {
+  thermo_kernel<<<n, kThermoThreads, 0, st>>>(j, betas, out);
   launches_add(1);
   return cudaGetLastError();
 }

@@ -33,6 +33,7 @@ def _compare_weights(g, o):
     assert np.abs(Wg - Wo).max() <= W_TOL
     assert np.array_equal(Wg, Wo)            # same operations, same order: same bits
     assert np.array_equal(g.table, o.table)
+    assert np.array_equal(g.visited, o.visited)
 
 
 def _run_parity(L, p, S, iters, start, seed, weights=None, shape=None, M_total=0):
