@@ -434,20 +434,24 @@ int mc_batch_run(mc_job** jobs, int n_jobs, int iterations, int64_t n_sweeps, in
     saved[i] = jobs[i]->stream;
     jobs[i]->stream = st;
   }
-  // shapes for the fused launch: the job's own shape when it fits, else the
-  // block shape of the fused launch with the job's chains per warp
+  // shapes for the fused launch: full warps (as many chains per warp as fit
+  // beside the threshold table).  A round takes as long as its slowest
+  // chain either way, and full warps let every job's blocks be resident at
+  // once, so the fused round lasts as long as the longest job's, not the sum.
   std::vector<LaunchShape> bshape(n_jobs);
   std::vector<char> fused(n_jobs, 0);
   for (int i = 0; i < n_jobs && mode > 0; ++i) {
-    LaunchShape s = jobs[i]->shape;
-    if (!mcgpu::batch_supported(jobs[i]->L, s)) {
-      s.placement = jobs[i]->L <= 32 ? mcgpu::kPlaceReg : mcgpu::kPlaceSmem;
-      s.wpb = mcgpu::kBatchWarps;
-      while (s.cpw > 1 && !mcgpu::batch_supported(jobs[i]->L, s)) s.cpw >>= 1;
-    }
+    LaunchShape s{jobs[i]->L <= 32 ? mcgpu::kPlaceReg : mcgpu::kPlaceSmem, std::min(32, jobs[i]->p),
+                  mcgpu::kBatchWarps};
+    while (s.cpw > 1 && !mcgpu::batch_supported(jobs[i]->L, s)) s.cpw >>= 1;
     bshape[i] = s;
     fused[i] = mcgpu::batch_supported(jobs[i]->L, s) ? 1 : 0;
   }
+  // fused blocks in order of decreasing work per chain (N), so that the
+  // longest chains start first
+  std::vector<int> order(n_jobs);
+  for (int i = 0; i < n_jobs; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a]->N > jobs[b]->N; });
   int rc = MC_OK;
   for (int i = 0; i < n_jobs && rc == MC_OK; ++i) {  // no allocation inside a capture
     if (jobs[i]->trace_on) rc = ensure_trace(jobs[i], n_sweeps);
@@ -466,7 +470,8 @@ int mc_batch_run(mc_job** jobs, int n_jobs, int iterations, int64_t n_sweeps, in
     P.n = 0;
     size_t smem = 0;
     int blocks = 0;
-    for (int i = 0; i < n_jobs && rc == MC_OK; ++i) {
+    for (int oi = 0; oi < n_jobs && rc == MC_OK; ++oi) {
+      const int i = order[oi];
       uint64_t t0 = 0;
       if ((rc = round_prepare(jobs[i], n_sweeps, &t0))) break;
       cudaError_t e = cudaSuccess;
