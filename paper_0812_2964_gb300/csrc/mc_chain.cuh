@@ -32,29 +32,68 @@ struct Prefetch {
   uint64_t blk;
 };
 
+//
+// GL > 1: a group of GL consecutive lanes (aligned) shares one chain and runs
+// its sweep in lockstep on identical data; lane gi of the group computes
+// Philox blocks gi, gi + GL, ... of the word and the group exchanges them by
+// shuffles, so a warp with few chains spends 8 / GL Philox evaluations per
+// word instead of 8 (the sweep's other work is the same for every lane).
+template <int GL = 1>
 __device__ __forceinline__ void philox_fill(uint32_t (&U)[32], const int n, const uint64_t blk, const uint32_t chain,
                                             const uint32_t k0, const uint32_t k1) {
+  if constexpr (GL == 1) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    if (4 * q < n) {
-      const uint64_t b = blk + static_cast<uint64_t>(q);
-      const uint4 r =
-          philox4x32_10(make_uint4(static_cast<uint32_t>(b), static_cast<uint32_t>(b >> 32), chain, kTagFlip), k0, k1);
-      U[4 * q + 0] = r.x;
-      U[4 * q + 1] = r.y;
-      U[4 * q + 2] = r.z;
-      U[4 * q + 3] = r.w;
+    for (int q = 0; q < 8; ++q) {
+      if (4 * q < n) {
+        const uint64_t b = blk + static_cast<uint64_t>(q);
+        const uint4 r =
+            philox4x32_10(make_uint4(static_cast<uint32_t>(b), static_cast<uint32_t>(b >> 32), chain, kTagFlip), k0, k1);
+        U[4 * q + 0] = r.x;
+        U[4 * q + 1] = r.y;
+        U[4 * q + 2] = r.z;
+        U[4 * q + 3] = r.w;
+      }
     }
+  } else {
+#ifdef __CUDACC__
+    static_assert(GL == 2 || GL == 4 || GL == 8, "lane groups of 2, 4 or 8");
+    constexpr int R = 8 / GL;
+    const int lane = static_cast<int>(threadIdx.x & 31u);
+    const int gi = lane & (GL - 1);
+    const int gbase = lane - gi;
+    const unsigned mask = ((1u << GL) - 1u) << gbase;
+    uint4 r[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int q = gi + t * GL;
+      r[t] = make_uint4(0u, 0u, 0u, 0u);
+      if (4 * q < n) {
+        const uint64_t b = blk + static_cast<uint64_t>(q);
+        r[t] = philox4x32_10(make_uint4(static_cast<uint32_t>(b), static_cast<uint32_t>(b >> 32), chain, kTagFlip), k0,
+                             k1);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < R; ++t)
+#pragma unroll
+      for (int sl = 0; sl < GL; ++sl) {
+        const int q = sl + t * GL;
+        U[4 * q + 0] = __shfl_sync(mask, r[t].x, gbase + sl);
+        U[4 * q + 1] = __shfl_sync(mask, r[t].y, gbase + sl);
+        U[4 * q + 2] = __shfl_sync(mask, r[t].z, gbase + sl);
+        U[4 * q + 3] = __shfl_sync(mask, r[t].w, gbase + sl);
+      }
+#endif
   }
 }
 
 // Start a chain's attempt stream at attempt t0 (a multiple of 4).
-template <int WD>
+template <int WD, int GL = 1>
 __device__ __forceinline__ void prefetch_init(Prefetch& pf, const int L, const uint64_t t0, const uint32_t chain,
                                               const uint32_t k0, const uint32_t k1) {
   const int lw = L - 32 * (WD - 1);
   const int n0 = (WD == 1) ? lw : 32;
-  philox_fill(pf.U, n0, t0 >> 2, chain, k0, k1);
+  philox_fill<GL>(pf.U, n0, t0 >> 2, chain, k0, k1);
   pf.blk = (t0 >> 2) + static_cast<uint64_t>(n0 / 4);
 }
 
@@ -109,7 +148,7 @@ __device__ __forceinline__ uint32_t spread4(uint32_t n) { return (n * 0x00204081
 // both flips of site b are loaded while site b is resolved, from the level
 // before site b.  Accepted flips accumulate in a mask applied at the word's
 // end; the left neighbour's flip is tracked in f.
-template <int WD, class Hook>
+template <int WD, int GL = 1, class Hook>
 __device__ __forceinline__ void sweep_row(uint32_t (&cur)[WD], const uint32_t (&up)[WD],
                                           const uint32_t (&dn)[WD], const int L, int& m,
                                           const uint32_t* __restrict__ T, const int np1, Prefetch& pf,
@@ -140,7 +179,7 @@ __device__ __forceinline__ void sweep_row(uint32_t (&cur)[WD], const uint32_t (&
 #pragma unroll
     for (int i = 0; i < 32; ++i) u[i] = pf.U[i];
     const int nb_next = (w + 1 < WD) ? ((w + 2 < WD) ? 32 : lw) : ((WD == 1) ? lw : 32);
-    philox_fill(pf.U, nb_next, pf.blk, chain, k0, k1);
+    philox_fill<GL>(pf.U, nb_next, pf.blk, chain, k0, k1);
     pf.blk += static_cast<uint64_t>(nb_next / 4);
     // packed per-site bytes
     uint32_t A0[8], D[8];
@@ -220,9 +259,9 @@ __device__ __forceinline__ void sweep_row(uint32_t (&cur)[WD], const uint32_t (&
 // shared-memory histogram (one reduction, no branch).
 struct GenHook {
   uint32_t* hist;
-  uint32_t run;  // unused; kept for a uniform hook interface
+  uint32_t inc;  // 1; 0 for the lanes of a lane group that only help (one count per chain)
   __device__ __forceinline__ void word(int) {}
-  __device__ __forceinline__ void sample(int m4, int) { red_shared_add(hist, m4, 1u); }
+  __device__ __forceinline__ void sample(int m4, int) { red_shared_add(hist, m4, inc); }
   __device__ __forceinline__ void flush(int) {}
 };
 

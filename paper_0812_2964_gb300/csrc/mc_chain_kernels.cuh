@@ -39,7 +39,7 @@ struct RegRunner {
 #pragma unroll
     for (int y = 0; y < L; ++y) R[y] = g[y * stride];
   }
-  template <bool EARLY, class Hook>
+  template <bool EARLY, int GL = 1, class Hook>
   __device__ __forceinline__ void sweep(int& m, Prefetch& pf, const uint32_t* __restrict__ T, int np1,
                                         uint32_t chain, uint32_t k0, uint32_t k1, Hook& hk) {
 #pragma unroll 1
@@ -47,7 +47,7 @@ struct RegRunner {
       uint32_t cur[1] = {R[0]};
       const uint32_t up[1] = {R[L - 1]};
       const uint32_t dn[1] = {R[1]};
-      sweep_row<1>(cur, up, dn, L, m, T, np1, pf, chain, k0, k1, hk);
+      sweep_row<1, GL>(cur, up, dn, L, m, T, np1, pf, chain, k0, k1, hk);
 #pragma unroll
       for (int i = 0; i < L - 1; ++i) R[i] = R[i + 1];
       R[L - 1] = cur[0];
@@ -81,7 +81,7 @@ struct SmemRunner {
     const int L = len();
     for (int i = 0; i < L * WD; ++i) lat[i * stride] = g[i * gstride];
   }
-  template <bool EARLY, class Hook>
+  template <bool EARLY, int GL = 1, class Hook>
   __device__ __forceinline__ void sweep(int& m, Prefetch& pf, const uint32_t* __restrict__ T, int np1,
                                         uint32_t chain, uint32_t k0, uint32_t k1, Hook& hk) {
     const int L = len();
@@ -95,7 +95,7 @@ struct SmemRunner {
         up[w] = lat[(ym * WD + w) * stride];
         dn[w] = lat[(yp * WD + w) * stride];
       }
-      sweep_row<WD>(cur, up, dn, L, m, T, np1, pf, chain, k0, k1, hk);
+      sweep_row<WD, GL>(cur, up, dn, L, m, T, np1, pf, chain, k0, k1, hk);
 #pragma unroll
       for (int w = 0; w < WD; ++w) lat[(y * WD + w) * stride] = cur[w];
       if constexpr (EARLY) {
@@ -125,11 +125,14 @@ struct BlockCtx {
   uint32_t* lat;
   int chain, lane, warp, slot, nslot;
   bool active;
+  bool owner;  // the lane that writes the chain's results (first of its lane group)
 };
 
+// Lanes per chain gl (a power of two; 1 except in the generation kernel's
+// lane-group variant): lane l of a warp works on the warp's chain l / gl.
 template <bool TSMEM>
 __device__ __forceinline__ BlockCtx block_setup(const DevJob& j, const SmemPlan& sp, int cpw, int first_chain,
-                                                bool zero_hist) {
+                                                bool zero_hist, int gl = 1) {
   extern __shared__ __align__(16) uint32_t smem[];
   BlockCtx b;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -142,10 +145,12 @@ __device__ __forceinline__ BlockCtx block_setup(const DevJob& j, const SmemPlan&
   b.lat = smem + sp.table_words + sp.hist_words;
   b.lane = tid & 31;
   b.warp = tid >> 5;
-  b.slot = b.warp * cpw + b.lane;
+  const int sub = b.lane / gl;
+  b.slot = b.warp * cpw + sub;
   b.nslot = (nthr >> 5) * cpw;
   b.chain = first_chain + b.slot;
-  b.active = b.lane < cpw && b.chain < j.p;
+  b.active = sub < cpw && b.chain < j.p;
+  b.owner = b.active && (b.lane % gl) == 0;
   return b;
 }
 
@@ -174,33 +179,43 @@ struct RunnerFactorySmem {
 // round histogram hgen.  trace[s][c] = energy after sweep s.
 // (The body is a device function so that the batched launch can run it for
 // one of several jobs per block.)
-template <class Factory, bool TSMEM>
+//
+// GL > 1 (lattice in shared memory, few chains per warp): the GL lanes of a
+// lane group share one chain -- same lattice column, same uniforms (split
+// between them, see philox_fill) -- and only the group's first lane writes
+// counts, checkpoints, trace and the final state.
+template <class Factory, bool TSMEM, int GL = 1>
 __device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const uint64_t t0, const int64_t S,
                                          const int64_t flushF, const int do_trace, const int block) {
   const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, true);
   const int first = block * (blockDim.x >> 5) * cpw;
-  BlockCtx b = block_setup<TSMEM>(j, sp, cpw, first, true);
+  BlockCtx b = block_setup<TSMEM>(j, sp, cpw, first, true, GL);
   auto run = Factory::make(b, j.L);
   __syncthreads();
   int m = 0;
   Prefetch pf;
-  GenHook hk{b.hist, 0u};
+  GenHook hk{b.hist, b.owner ? 1u : 0u};
   if (b.active) {
     run.load(j.spins + static_cast<size_t>(b.chain) * j.L * j.wd);
     m = j.m[b.chain];
-    prefetch_init<decltype(run)::WD>(pf, j.L, t0, static_cast<uint32_t>(b.chain), j.key0, j.key1);
+    prefetch_init<decltype(run)::WD, GL>(pf, j.L, t0, static_cast<uint32_t>(b.chain), j.key0, j.key1);
   }
   const size_t lw = static_cast<size_t>(j.L) * j.wd;
+  // the lanes of the warp's working lane groups: they meet again after every
+  // write that only a group's first lane makes, before the next shuffles
+  const unsigned amask = __ballot_sync(0xFFFFFFFFu, b.active);
   for (int64_t s = 0; s < S; ++s) {
     if (b.active) {
-      if (j.ckpt && (s % j.ck_C) == 0) {
+      if (j.ckpt && (s % j.ck_C) == 0 && b.owner) {
         // lattice and level at the start of segment s / C, for the joint's replays
         const size_t seg = static_cast<size_t>(s / j.ck_C);
         run.save_strided(j.ckpt + seg * lw * j.p + b.chain, static_cast<size_t>(j.p));
         j.ckm[seg * j.p + b.chain] = m;
       }
-      run.template sweep<false>(m, pf, b.T, j.np1, static_cast<uint32_t>(b.chain), j.key0, j.key1, hk);
-      if (do_trace) j.trace[s * j.p + b.chain] = 4 * m - 2 * j.N;
+      if constexpr (GL > 1) __syncwarp(amask);
+      run.template sweep<false, GL>(m, pf, b.T, j.np1, static_cast<uint32_t>(b.chain), j.key0, j.key1, hk);
+      if (do_trace && b.owner) j.trace[s * j.p + b.chain] = 4 * m - 2 * j.N;
+      if constexpr (GL > 1) __syncwarp(amask);
     }
     if (flushF > 0 && (s + 1) % flushF == 0 && s + 1 < S) {
       if (b.active) hk.flush(m);
@@ -216,7 +231,7 @@ __device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const u
       __syncthreads();
     }
   }
-  if (b.active) {
+  if (b.owner) {
     hk.flush(m);
     run.store(j.spins + static_cast<size_t>(b.chain) * j.L * j.wd);
     j.m[b.chain] = m;
@@ -229,10 +244,10 @@ __device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const u
   }
 }
 
-template <class Factory, bool TSMEM>
+template <class Factory, bool TSMEM, int GL = 1>
 __global__ void __launch_bounds__(128) gen_kernel(const DevJob j, const int cpw, const uint64_t t0,
                                                   const int64_t S, const int64_t flushF, const int do_trace) {
-  gen_body<Factory, TSMEM>(j, cpw, t0, S, flushF, do_trace, blockIdx.x);
+  gen_body<Factory, TSMEM, GL>(j, cpw, t0, S, flushF, do_trace, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ joint: replays
@@ -619,7 +634,10 @@ template <class F, bool TS>
 inline cudaError_t launch_gen_t(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S, bool trace,
                                 cudaStream_t st) {
   const size_t bytes = plan_bytes(j.L, s, TS, true);
-  auto kern = gen_kernel<F, TS>;
+  // lattice in shared memory with at most 8 chains a warp: lane groups of 4
+  auto kern = gen_kernel<F, TS, 1>;
+  if constexpr (F::kPlacement == kPlaceSmem)
+    if (s.cpw <= 8) kern = gen_kernel<F, TS, 4>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
   if (e != cudaSuccess) return e;
   const int per_block = s.cpw * s.wpb;
