@@ -467,6 +467,61 @@ def run_serving(args):
     return 0
 
 
+def run_fig2(args):
+    """The Fig. 2 experiment shape (Sec. 5): L = 20, p = 32 short chains, the
+    weight iteration run twice -- chains joined by detailed balance
+    (mc_join) and simply concatenated (mc_join_naive) -- each iteration
+    collecting M_total samples in rounds of M_node attempts per chain; then
+    E/N by Eq. (reweighting2) against the exact finite-lattice values.
+    M_node is one sweep (N = 400 attempts; the paper's 100 is a partial
+    sweep, which this library's rounds do not make)."""
+    import torch
+
+    import paper_0812_2964_gb300 as mc
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from exact import exact_thermo
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    mc.build()
+    L, p, S = 20, 32, 1
+    N = L * L
+    M_total = args.mtotal
+    iters = args.iters
+    betas = [0.1, 0.2, 0.3, 0.35, 0.4, 0.4406867935097715, 0.5, 0.6, 0.8, 1.0]
+    exact = [exact_thermo(L, b)[0] / N for b in betas]
+    out = {}
+    for name, naive in (("detailed balance", False), ("no detailed balance", True)):
+        job = mc.Job(L, p, 10 + rank, 1)
+        rounds = 0
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            got = 0
+            while got < M_total:
+                job.run_sweeps(S)
+                got += job.join_naive() if naive else job.join()
+                rounds += 1
+            job.update_weights()
+        el = time.perf_counter() - t0
+        E = job.thermo(betas)[:, 0] / N
+        dev = [float(e - x) for e, x in zip(E, exact)]
+        out[name] = {"E_per_site": [float(e) for e in E], "deviation": dev,
+                     "max_abs_dev_beta_le_0.44": max(abs(d) for b, d in zip(betas, dev) if b <= 0.45),
+                     "max_abs_dev_beta_gt_0.44": max(abs(d) for b, d in zip(betas, dev) if b > 0.45),
+                     "rounds": rounds, "seconds": el}
+        job.close()
+    line = {"metric": "fig2: E/N deviation from the exact L=20 values", "unit": "energy per site",
+            "value": out["detailed balance"]["max_abs_dev_beta_le_0.44"], "higher_is_better": False,
+            "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "fig2", "L": L, "chains": p, "M_node_attempts": S * N, "M_total": M_total,
+                       "iterations": iters, "betas": betas},
+            "exact_E_per_site": exact, "runs": out}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -474,7 +529,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", default=WORKLOAD,
-                    help="L32_p16384 (default), L64_p4096, L128_p1024, L8_p64, batch_uneven or serving")
+                    help="L32_p16384 (default), L64_p4096, L128_p1024, L8_p64, batch_uneven, serving or fig2")
     ap.add_argument("--sweeps", type=int, default=0, help="override sweeps per iteration")
     ap.add_argument("--tune", action="store_true", help="pick the launch shape with mc_autotune first")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -483,6 +538,8 @@ def main(argv=None):
     ap.add_argument("--jobs", type=int, default=400, help="serving: jobs in the arrival stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=64, help="serving: server slots")
+    ap.add_argument("--mtotal", type=int, default=10_000_000, help="fig2: samples per weight iteration")
+    ap.add_argument("--iters", type=int, default=40, help="fig2: weight iterations")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -490,6 +547,8 @@ def main(argv=None):
         return run_batch(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "fig2":
+        return run_fig2(args)
     return run_gpu(args)
 
 
