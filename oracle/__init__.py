@@ -100,6 +100,8 @@ def _declare(L):
         "or_get_samples": (None, [c.c_void_p, _i32p]),
         "or_set_samples": (c.c_int, [c.c_void_p, c.c_int64, _i32p]),
         "or_get_visited": (None, [c.c_void_p, _u8p]),
+        "or_set_join_order": (None, [c.c_void_p, c.c_int]),
+        "or_get_order": (None, [c.c_void_p, _i32p]),
         "or_thermo": (None, [c.c_int, _dp, _u8p, _dp, c.c_int, _dp]),
     }
     for name, (res, args) in sig.items():
@@ -297,6 +299,15 @@ class Job:
     @property
     def t(self):
         return int(lib().or_get_t(self._h))
+
+    def set_join_order(self, mode: int):
+        lib().or_set_join_order(self._h, int(mode))
+
+    @property
+    def order(self):
+        out = np.zeros(self.p, dtype=np.int32)
+        lib().or_get_order(self._h, _p(out, _i32p))
+        return out
 
     @property
     def visited(self):

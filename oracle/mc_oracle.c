@@ -337,6 +337,8 @@ struct or_job {
     int32_t *trace;     /* [p][S] level after each sweep */
     int64_t *k;         /* [p] first kept sample of the last joint (0 = none) */
     uint8_t *visited;   /* [N+1] 1 once a weight update has seen h > 0 there */
+    int join_order;     /* 0: chains joined in index order; 1: by final energy */
+    int32_t *order;     /* [p] chain at each position of the last joint */
 };
 
 or_job *or_create(int L, int p, uint64_t seed, int start)
@@ -354,6 +356,8 @@ or_job *or_create(int L, int p, uint64_t seed, int start)
     j->h = (int64_t *)calloc((size_t)j->N + 1, sizeof(int64_t));     /* step 1: h(E) = 0 */
     j->k = (int64_t *)calloc((size_t)p, sizeof(int64_t));
     j->visited = (uint8_t *)calloc((size_t)j->N + 1, 1);
+    j->order = (int32_t *)malloc(sizeof(int32_t) * (size_t)p);
+    for (int c = 0; c < p; ++c) j->order[c] = c;
     for (int c = 0; c < p; ++c) {
         int8_t *s = j->spins + (size_t)c * j->N;
         or_init_lattice(s, L, seed, (uint32_t)c, start);
@@ -367,7 +371,7 @@ void or_free(or_job *j)
 {
     if (!j) return;
     free(j->spins); free(j->m); free(j->W); free(j->T); free(j->h);
-    free(j->samples); free(j->trace); free(j->k); free(j->visited);
+    free(j->samples); free(j->trace); free(j->k); free(j->visited); free(j->order);
     free(j);
 }
 
@@ -428,11 +432,38 @@ int or_run_round(or_job *j, int64_t S, int nthreads)
  * nothing to check against and node 0's chain is kept whole.
  * Returns the number of configurations kept in this round.
  */
+/* Order of the chains at the joint.  Index order, or (the energy-ordered
+ * joining the paper proposes at the end of Sec. 2 to raise acceptance, with
+ * the order left open there) ascending by the energy of each chain's last
+ * generated configuration, equal energies in index order. */
+static const int32_t *g_sort_levels;
+static int cmp_by_level(const void *a, const void *b)
+{
+    const int32_t ia = *(const int32_t *)a, ib = *(const int32_t *)b;
+    const int32_t la = g_sort_levels[ia], lb = g_sort_levels[ib];
+    if (la != lb) return la < lb ? -1 : 1;
+    return ia < ib ? -1 : (ia > ib ? 1 : 0);
+}
+
+static void joint_order(or_job *j, int64_t M)
+{
+    for (int c = 0; c < j->p; ++c) j->order[c] = c;
+    if (j->join_order != 1) return;
+    int32_t *last = (int32_t *)malloc(sizeof(int32_t) * (size_t)j->p);
+    for (int c = 0; c < j->p; ++c) last[c] = j->samples[(size_t)c * (size_t)M + (size_t)(M - 1)];
+    g_sort_levels = last;
+    qsort(j->order, (size_t)j->p, sizeof(int32_t), cmp_by_level);
+    g_sort_levels = NULL;
+    free(last);
+}
+
 int64_t or_join(or_job *j)
 {
     int64_t M = j->last_S * (int64_t)j->N;
     int64_t joined = 0;
-    for (int i = 0; i < j->p; ++i) {
+    joint_order(j, M);
+    for (int q = 0; q < j->p; ++q) {
+        const int i = j->order[q];
         const int32_t *lev = j->samples + (size_t)i * (size_t)M;
         int64_t k;
         if (!j->carry_valid)
@@ -441,7 +472,7 @@ int64_t or_join(or_job *j)
             k = or_joint_scan(lev, M, j->W, j->carry, j->seed, j->r, (uint32_t)i);
         j->k[i] = k;
         if (k > 0) {
-            for (int64_t q = k - 1; q < M; ++q) j->h[lev[q]] += 1;   /* h += h_local */
+            for (int64_t t = k - 1; t < M; ++t) j->h[lev[t]] += 1;   /* h += h_local */
             joined += M - k + 1;
             j->carry = lev[M - 1];
             j->carry_valid = 1;
@@ -456,16 +487,21 @@ int64_t or_join(or_job *j)
 int64_t or_join_naive(or_job *j)
 {
     int64_t M = j->last_S * (int64_t)j->N;
-    for (int i = 0; i < j->p; ++i) {
+    joint_order(j, M);
+    for (int q = 0; q < j->p; ++q) {
+        const int i = j->order[q];
         const int32_t *lev = j->samples + (size_t)i * (size_t)M;
         j->k[i] = 1;
-        for (int64_t q = 0; q < M; ++q) j->h[lev[q]] += 1;
+        for (int64_t t = 0; t < M; ++t) j->h[lev[t]] += 1;
         j->carry = lev[M - 1];
         j->carry_valid = 1;
     }
     j->r += 1;
     return M * (int64_t)j->p;
 }
+
+void or_set_join_order(or_job *j, int mode) { j->join_order = mode; }
+void or_get_order(const or_job *j, int32_t *order) { memcpy(order, j->order, sizeof(int32_t) * (size_t)j->p); }
 
 /* Eq. (new_weight) in logarithms: w <- w / h where h > 0, i.e. W -= ln h;
  * then h is cleared for the next iteration. */

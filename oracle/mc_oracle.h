@@ -66,6 +66,9 @@ void    or_free(or_job *j);
 int     or_run_round(or_job *j, int64_t S, int nthreads);
 int64_t or_join(or_job *j);
 int64_t or_join_naive(or_job *j);
+/* joint order: 0 chain index (default), 1 ascending final energy (ties by index) */
+void    or_set_join_order(or_job *j, int mode);
+void    or_get_order(const or_job *j, int32_t *order);   /* [p] chain at each position */
 void    or_update_weights(or_job *j);
 int64_t or_iteration(or_job *j, int64_t S, int64_t M_total, int nthreads);
 

@@ -202,3 +202,47 @@ def test_joined_chain_is_flat_under_exact_weights():
     err = per_round.std(axis=0, ddof=1) / np.sqrt(len(per_round))
     target = 1.0 / reach.sum()
     assert (np.abs(mean - target) < 5 * err + 1e-4).all(), (mean, err)
+
+
+def test_energy_ordered_joint_hand_made():
+    # W rises steeply with the level: a joint to a lower level fails (d <= -30,
+    # threshold 0, and no uniform is 0), to an equal or higher level it passes
+    L, N, p, S = 4, 16, 5, 1
+    levels = [5, 1, 4, 2, 3]
+    W = 30.0 * np.arange(N + 1)
+    results = {}
+    for mode in (0, 1):
+        job, M = _crafted_job(p, S, L)
+        job.set_join_order(mode)
+        job.weights = W
+        samp = np.array([[lv] * M for lv in levels], np.int32)
+        for i in range(p):
+            assert all(_ju(0, i, k) != 0 for k in range(1, M + 1))
+        job.set_samples(S, samp)
+        results[mode] = (job.join(), list(job.k), list(job.order), job.carry, job.hist.copy())
+    # index order: chain 0 (level 5) kept whole, every later chain lies below the carry
+    assert results[0][:4] == (M, [1, 0, 0, 0, 0], [0, 1, 2, 3, 4], 5)
+    # ascending final energy: 1, 3, 4, 2, 0 -- each joint goes up, all kept whole
+    assert results[1][:4] == (p * M, [1, 1, 1, 1, 1], [1, 3, 4, 2, 0], 5)
+    assert (results[1][4] == np.bincount(levels, minlength=N + 1) * M).all()
+
+
+def test_energy_order_ties_and_invariants():
+    L, p, S = 6, 12, 3
+    N = L * L
+    o = oracle.Job(L, p, 21, 1)
+    o.set_join_order(1)
+    o.weights = np.random.default_rng(4).normal(0, 2.0, N + 1)
+    for _ in range(4):
+        o.run_round(S, 4)
+        last = o.levels.copy()
+        joined = o.join()
+        order = o.order
+        assert list(order) == list(np.lexsort((np.arange(p), last)))   # by level, ties by index
+        k = o.k
+        M = S * N
+        assert joined == sum(M - kk + 1 for kk in k if kk > 0) == o.hist.sum()
+        kept_in_order = [c for c in order if k[c] > 0]
+        if kept_in_order:
+            assert o.carry == last[kept_in_order[-1]]
+        o.update_weights()
