@@ -213,6 +213,8 @@ def run_gpu(args):
     job = mc.Job(w.L, p, w.seed + rank, w.start)
     job.set_stream(stream.cuda_stream)
     job.set_trace(True)
+    if args.join_order:
+        job.set_join_order(args.join_order)
     if args.tune:
         job.autotune(probe_sweeps=max(1, min(S, 4_000_000 // N)))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
@@ -317,7 +319,8 @@ def run_gpu(args):
                    "launch": {"placement": ["registers", "shared"][info["placement"]],
                               "chains_per_warp": info["chains_per_warp"],
                               "warps_per_block": info["warps_per_block"]},
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "join_order": ["chain index", "ascending final energy"][args.join_order]},
         "kept_fraction": kept / (args.steps * p * M),
         "raw_attempts_per_s": args.steps * p * M * world / t_max,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
@@ -538,6 +541,8 @@ def main(argv=None):
     ap.add_argument("--jobs", type=int, default=400, help="serving: jobs in the arrival stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=64, help="serving: server slots")
+    ap.add_argument("--join-order", type=int, default=0,
+                    help="0: chains joined in index order; 1: by ascending final energy (end of Sec. 2)")
     ap.add_argument("--mtotal", type=int, default=10_000_000, help="fig2: samples per weight iteration")
     ap.add_argument("--iters", type=int, default=40, help="fig2: weight iterations")
     args = ap.parse_args(argv)

@@ -124,6 +124,18 @@ int mc_update_weights(mc_job *job);
 int mc_get_weights(mc_job *job, double *out, int n);
 int mc_set_weights(mc_job *job, const double *w, int n);
 
+/* Order of the chains at the joint (Sec. 2 steps 3-5).  mode 0 (default):
+ * chain index.  mode 1: energy-ordered joining, which the end of Sec. 2
+ * proposes to raise the acceptance at the joints and leaves unspecified --
+ * here the chains are joined in ascending order of the energy of their last
+ * generated configuration, equal energies by chain index; the joint's
+ * uniforms keep their chain's index.  It changes which samples are kept (a
+ * different, still exact, dynamics).  MC_EINVAL for another mode, MC_ESTATE
+ * while a round is pending.  mc_get_order: out[q] = chain at position q of
+ * the last joint (n = n_chains; synchronises). */
+int mc_set_join_order(mc_job *job, int mode);
+int mc_get_order(mc_job *job, int32_t *out, int n);
+
 /* Levels the weight iteration has visited: out[m] = 1 once a weight update
  * (mc_update_weights) saw h[m] > 0, else 0; n = N+1.  These are the
  * energies the statistical averages sum over.  mc_set_visited restores a

@@ -19,7 +19,8 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_init", "mc_free", "mc_set_stream", "mc_set_trace", "mc_run_sweeps", "mc_join",
     "mc_join_naive", "mc_histogram", "mc_update_weights", "mc_get_weights", "mc_set_weights",
     "mc_get_table", "mc_get_spins", "mc_set_spins", "mc_get_energies", "mc_get_trace",
-    "mc_get_trace_chain", "mc_get_visited", "mc_set_visited", "mc_thermo",
+    "mc_get_trace_chain", "mc_get_visited", "mc_set_visited", "mc_thermo", "mc_set_join_order",
+    "mc_get_order",
     "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error",
     "mc_generate_noalloc", "mc_autotune", "mc_batch_run",
     "mc_job_device_bytes", "mc_server_create", "mc_server_submit", "mc_server_poll", "mc_server_wait",
@@ -114,6 +115,8 @@ def lib():
             "mc_get_visited": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
             "mc_set_visited": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
             "mc_thermo": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
+            "mc_set_join_order": (ctypes.c_int, [_vp, ctypes.c_int]),
+            "mc_get_order": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
             "mc_get_join": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
             "mc_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(mc_info)]),
             "mc_set_launch_shape": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -255,6 +258,16 @@ def mc_get_visited(job, out: np.ndarray):
 def mc_set_visited(job, v: np.ndarray):
     v = np.ascontiguousarray(v, dtype=np.uint8)
     _check(lib().mc_set_visited(job, _ptr(v), v.size))
+
+
+def mc_set_join_order(job, mode: int):
+    _check(lib().mc_set_join_order(job, int(mode)))
+
+
+def mc_get_order(job, out: np.ndarray):
+    assert out.dtype == np.int32 and out.flags.c_contiguous
+    _check(lib().mc_get_order(job, _ptr(out), out.size))
+    return out
 
 
 def mc_thermo(job, betas) -> np.ndarray:
@@ -410,6 +423,13 @@ class Job:
     @visited.setter
     def visited(self, v):
         mc_set_visited(self.h, v)
+
+    def set_join_order(self, mode: int):
+        mc_set_join_order(self.h, mode)
+
+    @property
+    def order(self):
+        return mc_get_order(self.h, np.zeros(self.p, np.int32))
 
     def thermo(self, betas):
         """E, C, F, S (columns) at each beta, from the current weight."""

@@ -191,6 +191,7 @@ int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
       (rc = dalloc(j, &d.offsets, n_chains)) || (rc = dalloc(j, &d.work, n_chains)) ||
       (rc = dalloc(j, &d.work2, n_chains)) ||
       (rc = dalloc(j, &d.lastacc, n_chains)) || (rc = dalloc(j, &d.summ, 3ull * n_chains)) || (rc = dalloc(j, &d.visited, np1)) ||
+      (rc = dalloc(j, &d.perm, n_chains)) || (rc = dalloc(j, &d.lvcnt, np1)) ||
       (rc = dalloc(j, &d.stats, mcgpu::kStatCount))) {
     free_all(j);
     delete j;
@@ -207,6 +208,7 @@ int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(d.offsets, 0, sizeof(int64_t) * n_chains, st);
   if (e == cudaSuccess) e = mcgpu::k_init_lattice(d, start, st);
   if (e == cudaSuccess) e = mcgpu::k_levels(d, st);
+  if (e == cudaSuccess) e = mcgpu::k_order(d, st);   // identity until ordered joining is chosen
   if (e == cudaSuccess) e = mcgpu::k_build_table(d, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
@@ -561,6 +563,21 @@ int mc_set_visited(mc_job* job, const uint8_t* in, int n) {
   return sync(job, "visited");
 }
 
+int mc_set_join_order(mc_job* job, int mode) {
+  if (int rc = check_job(job)) return rc;
+  if (mode != 0 && mode != 1) return fail(MC_EINVAL, "join order %d: 0 chain index, 1 ascending final energy", mode);
+  if (job->pending) return fail(MC_ESTATE, "round pending");
+  job->d.ordered = mode;
+  return MC_OK;
+}
+
+int mc_get_order(mc_job* job, int32_t* out, int n) {
+  if (int rc = check_job(job)) return rc;
+  if (!out || n != job->p) return fail(MC_EINVAL, "order needs n_chains entries");
+  MC_CUDA(cudaMemcpyAsync(out, job->d.perm, 4ull * n, cudaMemcpyDeviceToHost, job->stream), "order copy");
+  return sync(job, "order");
+}
+
 int mc_thermo(mc_job* job, const double* betas, int n_beta, double* out) {
   if (int rc = check_job(job)) return rc;
   if (!betas || !out || n_beta < 1 || n_beta > 65535) return fail(MC_EINVAL, "need 1..65535 betas and an output");
@@ -781,9 +798,9 @@ uint64_t mc_job_device_bytes(int L, int n_chains, int64_t sweeps) {
   const uint64_t N = static_cast<uint64_t>(L) * L, np1 = N + 1, wd = (L + 31) / 32;
   const uint64_t p = static_cast<uint64_t>(n_chains), lw = static_cast<uint64_t>(L) * wd, lat = p * lw;
   // as allocated by mc_init: spins, spins0, m, m0, W, T, h, hgen, dpre, k,
-  // xused, tj, offsets, work, work2, lastacc, summ, visited, stats
+  // xused, tj, offsets, work, work2, lastacc, summ, visited, perm, lvcnt, stats
   uint64_t b = lat * 4 * 2 + p * 4 * 2 + np1 * 8 + 5 * np1 * 4 + np1 * 8 * 3 + p * 8 + p * 4 + p * np1 * 4 +
-               p * 8 + p * 4 + p * 4 + p * 4 + p * 12 + np1 + mcgpu::kStatCount * 8;
+               p * 8 + p * 4 + p * 4 + p * 4 + p * 12 + np1 + p * 4 + np1 * 4 + mcgpu::kStatCount * 8;
   int K = 0, C = 0;
   round_segments(L * L, sweeps, &K, &C);
   return b + static_cast<uint64_t>(K) * p * (lw * 4 + 4 + 8 + 8);

@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(128) summary_kernel(const DevJob j, const int 
     const long long item = base + b.lane;
     if (b.lane < cpw && item < items) {
       const int seg = static_cast<int>(item / nchains);
-      const int i = f + static_cast<int>(item % nchains);
+      const int i = j.perm[f + static_cast<int>(item % nchains)];
       SummaryHook hk;
       hk.umin = j.tj + static_cast<size_t>(i) * j.np1;
       hk.k = static_cast<int64_t>(seg) * j.ck_C * j.N;
@@ -478,16 +478,16 @@ __global__ void __launch_bounds__(128) prefix_kernel(const DevJob j, const int c
   }
 }
 
-// Block-wide scan: out[i] = index of the last chain before i whose k > 0
-// (or -1).  Each thread takes a contiguous range of chains; s_tmp holds
-// blockDim.x ints.
+// Block-wide scan over positions of the joint: out[q] = the last position
+// before q whose chain (perm[]) has k > 0 (or -1).  Each thread takes a
+// contiguous range of positions; s_tmp holds blockDim.x ints.
 __device__ __forceinline__ void block_last_accepted(const DevJob& j, int* s_tmp, int32_t* out) {
   const int t = threadIdx.x, nt = blockDim.x;
   const int per = (j.p + nt - 1) / nt;
   const int lo = min(j.p, t * per), hi = min(j.p, lo + per);
   int last = -1;
   for (int i = lo; i < hi; ++i)
-    if (j.k[i] > 0) last = i;
+    if (j.k[j.perm[i]] > 0) last = i;
   s_tmp[t] = last;
   __syncthreads();
   for (int off = 1; off < nt; off <<= 1) {
@@ -499,7 +499,7 @@ __device__ __forceinline__ void block_last_accepted(const DevJob& j, int* s_tmp,
   int run = (t > 0) ? s_tmp[t - 1] : -1;  // exclusive prefix
   for (int i = lo; i < hi; ++i) {
     out[i] = run;
-    if (j.k[i] > 0) run = i;
+    if (j.k[j.perm[i]] > 0) run = i;
   }
   __syncthreads();
 }
@@ -526,9 +526,10 @@ __global__ void __launch_bounds__(128) resolve_kernel(const DevJob j, const int 
     __syncthreads();
     // list of chains whose input changed (j.work reused: first the scan
     // result, then the list, written after the scan result was consumed)
-    for (int i = threadIdx.x; i < j.p; i += blockDim.x) {
-      const int last = j.work[i];
-      const int x = (last >= 0) ? j.m[last] : carry_in;
+    for (int q = threadIdx.x; q < j.p; q += blockDim.x) {   // positions in the joint
+      const int last = j.work[q];
+      const int x = (last >= 0) ? j.m[j.perm[last]] : carry_in;
+      const int i = j.perm[q];
       if (x != j.xused[i]) {
         j.xused[i] = x;
         j.k[i] = -1;  // marked: to be searched again
@@ -578,12 +579,13 @@ __global__ void __launch_bounds__(128) resolve_kernel(const DevJob j, const int 
     }
     __syncthreads();
   }
-  // carry for the next round: the last level of the last chain that kept samples
+  // carry for the next round: the last level of the last chain (in joint
+  // order) that kept samples
   if (threadIdx.x == 0) {
     int last = -1;
-    for (int i = j.p - 1; i >= 0; --i)
-      if (j.k[i] > 0) {
-        last = i;
+    for (int q = j.p - 1; q >= 0; --q)
+      if (j.k[j.perm[q]] > 0) {
+        last = j.perm[q];
         break;
       }
     if (last >= 0) {

@@ -46,6 +46,9 @@ struct DevJob {
   int2* plist;         // [p*kcap] (chain, segment) work list of the prefix pass
   int32_t* summ;       // [3][p] summary pass: lowest and highest level visited, flag
   uint8_t* visited;    // [np1] 1 once a weight update has seen h > 0 at the level
+  int32_t* perm;       // [p] chain at each position of the joint (identity unless ordered)
+  int32_t* lvcnt;      // [np1] scratch of the energy ordering
+  int ordered;         // 1: chains joined by ascending final level (ties by index)
   int ck_C;            // sweeps per segment in the current round
   int ck_K;            // segments in the current round
   int kcap;            // segment capacity
@@ -74,6 +77,8 @@ enum StatIndex : int {
 
 // ---- kernels (mc_kernels.cu) ----
 cudaError_t k_init_lattice(const DevJob& j, int start, cudaStream_t st);
+// the joint order (perm) for the job's current levels and j.ordered
+cudaError_t k_order(const DevJob& j, cudaStream_t st);
 cudaError_t k_levels(const DevJob& j, cudaStream_t st);
 cudaError_t k_build_table(const DevJob& j, cudaStream_t st);
 cudaError_t k_update_weights(const DevJob& j, cudaStream_t st);

@@ -186,14 +186,73 @@ __global__ void tj_kernel(const DevJob j, const int32_t* __restrict__ list, cons
 // chain i-1 (chain 0 receives the carry from the previous round, or nothing
 // in the job's first round).
 __global__ void spec_inputs_kernel(const DevJob j) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= j.p) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // position in the joint
+  if (q >= j.p) return;
   int x;
-  if (i == 0)
+  if (q == 0)
     x = j.stats[kStatCarryValid] ? static_cast<int>(j.stats[kStatCarry]) : -1;
   else
-    x = j.m[i - 1];
-  j.xused[i] = x;
+    x = j.m[j.perm[q - 1]];
+  j.xused[j.perm[q]] = x;
+}
+
+// Joint order (one block): identity, or -- energy-ordered joining -- the
+// chains sorted by final level, equal levels in index order: a counting sort
+// whose scatter walks the chains in index order a warp at a time (ranks among
+// equal levels inside a warp from __match_any_sync).
+__global__ void __launch_bounds__(1024) order_kernel(const DevJob j) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  if (!j.ordered) {
+    for (int q = t; q < j.p; q += nt) j.perm[q] = q;
+    return;
+  }
+  __shared__ int s_part[1024];
+  for (int v = t; v < j.np1; v += nt) j.lvcnt[v] = 0;
+  __syncthreads();
+  for (int c = t; c < j.p; c += nt) atomicAdd(&j.lvcnt[j.m[c]], 1);
+  __syncthreads();
+  // exclusive scan of the counts: contiguous ranges per thread
+  const int per = (j.np1 + nt - 1) / nt;
+  const int lo = min(j.np1, t * per), hi = min(j.np1, lo + per);
+  int sum = 0;
+  for (int v = lo; v < hi; ++v) sum += j.lvcnt[v];
+  s_part[t] = sum;
+  __syncthreads();
+  for (int off = 1; off < nt; off <<= 1) {
+    const int a = (t >= off) ? s_part[t - off] : 0;
+    __syncthreads();
+    s_part[t] += a;
+    __syncthreads();
+  }
+  int run = s_part[t] - sum;
+  for (int v = lo; v < hi; ++v) {
+    const int c = j.lvcnt[v];
+    j.lvcnt[v] = run;
+    run += c;
+  }
+  __syncthreads();
+  // stable scatter
+  const int lane = t & 31, warp = t >> 5, nwarps = nt >> 5;
+  for (int base = 0; base < j.p; base += nt) {
+    const int c = base + t;
+    const bool act = c < j.p;
+    const unsigned amask = __ballot_sync(0xFFFFFFFFu, act);
+    int v = -1;
+    unsigned same = 0u;
+    if (act) {
+      v = j.m[c];
+      same = __match_any_sync(amask, v);
+    }
+    for (int w = 0; w < nwarps; ++w) {
+      if (warp == w && act) {
+        const int rank = __popc(same & ((1u << lane) - 1u));
+        j.perm[j.lvcnt[v] + rank] = c;
+        __syncwarp(amask);
+        if (rank == 0) j.lvcnt[v] += __popc(same);
+      }
+      __syncthreads();
+    }
+  }
 }
 
 // Segmented scan and histogram: kept length of chain i is M - k_i + 1 (0 if
@@ -208,10 +267,10 @@ __global__ void __launch_bounds__(1024) finalize_kernel(const DevJob j, const in
     j.dpre[m] = 0ull;
   }
   const int per = (j.p + nt - 1) / nt;
-  const int lo = min(j.p, t * per), hi = min(j.p, lo + per);
+  const int lo = min(j.p, t * per), hi = min(j.p, lo + per);  // positions in the joint
   long long sum = 0, rej = 0;
-  for (int i = lo; i < hi; ++i) {
-    const int64_t k = j.k[i];
+  for (int q = lo; q < hi; ++q) {
+    const int64_t k = j.k[j.perm[q]];
     sum += k > 0 ? (M - k + 1) : 0;
     rej += k > 0 ? 0 : 1;
   }
@@ -224,7 +283,8 @@ __global__ void __launch_bounds__(1024) finalize_kernel(const DevJob j, const in
     __syncthreads();
   }
   long long run = s_tmp[t] - sum;
-  for (int i = lo; i < hi; ++i) {
+  for (int q = lo; q < hi; ++q) {
+    const int i = j.perm[q];
     j.offsets[i] = run;
     const int64_t k = j.k[i];
     run += k > 0 ? (M - k + 1) : 0;
@@ -251,7 +311,7 @@ __global__ void naive_kernel(const DevJob j) {
     j.xused[i] = -1;
   }
   if (i == 0) {
-    j.stats[kStatCarry] = j.m[j.p - 1];
+    j.stats[kStatCarry] = j.m[j.perm[j.p - 1]];
     j.stats[kStatCarryValid] = 1;
     j.stats[kStatMismatch] = 0;
     j.stats[kStatPasses] = 0;
@@ -292,15 +352,16 @@ __global__ void __launch_bounds__(1024) mark_kernel(const DevJob j) {
   }
   __syncthreads();
   const int carry_in = j.stats[kStatCarryValid] ? static_cast<int>(j.stats[kStatCarry]) : -1;
-  for (int i = threadIdx.x; i < j.p; i += blockDim.x) {
-    const int last = j.lastacc[i];
-    const int x = (last >= 0) ? j.m[last] : carry_in;
+  for (int q = threadIdx.x; q < j.p; q += blockDim.x) {   // positions in the joint
+    const int last = j.lastacc[q];
+    const int x = (last >= 0) ? j.m[j.perm[last]] : carry_in;
+    const int i = j.perm[q];
     if (x != j.xused[i]) {
       j.xused[i] = x;
       j.k[i] = -1;
       for (int s2 = 0; s2 < j.ck_K; ++s2) j.first[static_cast<size_t>(i) * j.kcap + s2] = -1;
       j.work[atomicAdd(&s_count, 1)] = i;
-      atomicMin(&s_first, i);
+      atomicMin(&s_first, q);
     }
   }
   __syncthreads();
@@ -319,13 +380,15 @@ __global__ void __launch_bounds__(1024) mark_kernel(const DevJob j) {
 // rebuilt afterwards for the chains that still need a search) starts empty.
 __global__ void summary_init_kernel(const DevJob j) {
   if (j.stats[kStatPending] == 0) return;
-  const int f = static_cast<int>(j.stats[kStatFirstPending]);
+  const int f = static_cast<int>(j.stats[kStatFirstPending]);   // a position in the joint
   const long long n = static_cast<long long>(j.p - f) * j.np1;
-  uint32_t* base = j.tj + static_cast<size_t>(f) * j.np1;
   for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < n;
-       idx += static_cast<long long>(gridDim.x) * blockDim.x)
-    base[idx] = 0xFFFFFFFFu;
-  for (int i = f + blockIdx.x * blockDim.x + threadIdx.x; i < j.p; i += gridDim.x * blockDim.x) {
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int i = j.perm[f + static_cast<int>(idx / j.np1)];
+    j.tj[static_cast<size_t>(i) * j.np1 + static_cast<size_t>(idx % j.np1)] = 0xFFFFFFFFu;
+  }
+  for (int q = f + blockIdx.x * blockDim.x + threadIdx.x; q < j.p; q += gridDim.x * blockDim.x) {
+    const int i = j.perm[q];
     j.summ[i] = 0x7FFFFFFF;     // lowest level visited
     j.summ[j.p + i] = -1;       // highest level visited
     j.summ[2 * j.p + i] = 0;    // a level's minimum was 0xFFFFFFFF
@@ -353,15 +416,15 @@ __global__ void __launch_bounds__(1024) scan_kernel(const DevJob j) {
   const int t = threadIdx.x, nt = blockDim.x;
   const int f = static_cast<int>(j.stats[kStatFirstPending]);
   const int carry_in = j.stats[kStatCarryValid] ? static_cast<int>(j.stats[kStatCarry]) : -1;
-  int x = (j.lastacc[f] >= 0) ? j.m[j.lastacc[f]] : carry_in;
+  int x = (j.lastacc[f] >= 0) ? j.m[j.perm[j.lastacc[f]]] : carry_in;
   if (t == 0) s_count = 0;
-  int i = f, scanned = 0;
+  int i = f, scanned = 0;   // i: position in the joint
   bool stopped = false;
   for (int c0 = f; c0 < j.p && !stopped; c0 += kChunk) {
     const int n = min(kChunk, j.p - c0);
     __syncthreads();
     for (int q = t; q < n; q += nt) {
-      const int c = c0 + q;
+      const int c = j.perm[c0 + q];
       const int64_t kc = j.k[c];
       s_xu[q] = j.xused[c];
       s_ks[q] = kc > 0 ? 1 : (kc == 0 ? 0 : -1);
@@ -373,6 +436,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const DevJob j) {
     __syncthreads();
     for (int q = 0; q < n; ++q) {
       i = c0 + q;
+      const int ch = j.perm[i];
       const bool known = (x == s_xu[q] && s_ks[q] >= 0);
       bool acc;
       if (known) {
@@ -380,7 +444,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const DevJob j) {
       } else if (x < 0) {
         acc = true;  // no input yet: the chain is kept whole (k = 1)
       } else {
-        const uint32_t* um = j.tj + static_cast<size_t>(i) * j.np1;
+        const uint32_t* um = j.tj + static_cast<size_t>(ch) * j.np1;
         const double wx = j.W[x];
         const bool flag = s_fl[q] != 0;
         int hit = 0, amb = 0;
@@ -401,18 +465,18 @@ __global__ void __launch_bounds__(1024) scan_kernel(const DevJob j) {
       }
       if (!known) {
         if (t == 0) {
-          j.xused[i] = x;
+          j.xused[ch] = x;
           if (x < 0) {
-            j.k[i] = 1;
+            j.k[ch] = 1;
           } else if (acc) {
-            j.k[i] = -1;
-            j.work[s_count++] = i;
+            j.k[ch] = -1;
+            j.work[s_count++] = ch;
           } else {
-            j.k[i] = 0;
+            j.k[ch] = 0;
           }
         }
         if (acc && x >= 0)
-          for (int s2 = t; s2 < j.ck_K; s2 += nt) j.first[static_cast<size_t>(i) * j.kcap + s2] = -1;
+          for (int s2 = t; s2 < j.ck_K; s2 += nt) j.first[static_cast<size_t>(ch) * j.kcap + s2] = -1;
       }
       if (acc) x = s_m[q];
     }
@@ -422,7 +486,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const DevJob j) {
   // stopped early: chains still waiting for a search keep their inputs
   if (t == 0) {
     for (int q = i; q < j.p; ++q)
-      if (j.k[q] < 0) j.work[s_count++] = q;
+      if (j.k[j.perm[q]] < 0) j.work[s_count++] = j.perm[q];
     j.stats[kStatPending] = s_count;
     j.stats[kStatScanned] = scanned;
   }
@@ -515,10 +579,11 @@ static LaunchShape join_shape(int L, const LaunchShape& gen) {
 }
 
 cudaError_t join_prelude(const DevJob& j, cudaStream_t st) {
+  order_kernel<<<1, 1024, 0, st>>>(j);
   spec_inputs_kernel<<<blocks_for(j.p, 256), 256, 0, st>>>(j);
   clear_stats_kernel<<<256, 256, 0, st>>>(j);
   tj_kernel<<<blocks_for(static_cast<long long>(j.p) * j.np1, 256), 256, 0, st>>>(j, nullptr, j.p);
-  launches_add(3);
+  launches_add(4);
   return cudaGetLastError();
 }
 
@@ -667,12 +732,19 @@ cudaError_t k_generate(const DevJob& j, const LaunchShape& s, uint64_t t0, int64
 cudaError_t k_join(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S, uint32_t r, bool naive,
                    cudaStream_t st) {
   if (naive) {
+    order_kernel<<<1, 1024, 0, st>>>(j);
     naive_kernel<<<blocks_for(j.p, 256), 256, 0, st>>>(j);
     finalize_kernel<<<1, 1024, 0, st>>>(j, S);
-    launches_add(2);
+    launches_add(3);
     return cudaGetLastError();
   }
   return dispatch(j, join_shape(j.L, s), false, t0, S, false, r, st);
+}
+
+cudaError_t k_order(const DevJob& j, cudaStream_t st) {
+  order_kernel<<<1, 1024, 0, st>>>(j);
+  launches_add(1);
+  return cudaGetLastError();
 }
 
 cudaError_t k_init_lattice(const DevJob& j, int start, cudaStream_t st) {

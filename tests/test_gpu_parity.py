@@ -36,13 +36,16 @@ def _compare_weights(g, o):
     assert np.array_equal(g.visited, o.visited)
 
 
-def _run_parity(L, p, S, iters, start, seed, weights=None, shape=None, M_total=0):
+def _run_parity(L, p, S, iters, start, seed, weights=None, shape=None, M_total=0, order=0):
     N = L * L
     g = mc.Job(L, p, seed, start)
     if shape is not None:
         g.set_launch_shape(*shape)
     g.set_trace(True)
     o = oracle.Job(L, p, seed, start)
+    if order:
+        g.set_join_order(order)
+        o.set_join_order(order)
     if weights is not None:
         g.weights = weights
         o.weights = weights
@@ -59,6 +62,7 @@ def _run_parity(L, p, S, iters, start, seed, weights=None, shape=None, M_total=0
             jg, jo = g.join(), o.join()
             assert jg == jo
             assert np.array_equal(g.k, o.k)
+            assert np.array_equal(g.order, o.order)
             info = g.info()
             mism += info["last_mismatch"]
             assert info["carry_valid"] == 1
@@ -105,6 +109,17 @@ def test_launch_shape_large_lattice(shape):
 
 def test_rounds_until_M_total():
     _run_parity(16, 20, 2, 3, 1, seed=9, M_total=int(2.5 * 20 * 2 * 256))
+
+
+@pytest.mark.parametrize("L,p,S,scale", [(8, 40, 3, 12.0), (16, 300, 2, 6.0), (32, 130, 2, 4.0), (64, 20, 1, 8.0)])
+def test_energy_ordered_joint_matches_oracle(L, p, S, scale):
+    # energy-ordered joining (end of Sec. 2): chains joined by ascending final
+    # level; rough weights so that both resolution paths run
+    W = random_weights(L, seed=3 * L, scale=scale)
+    g, o, mism = _run_parity(L, p, S, 3, 1, seed=500 + L, weights=W, order=1)
+    order = g.order
+    lv = (g.energies.astype(np.int64) + 2 * L * L) // 4
+    assert list(order) == list(np.lexsort((np.arange(p), lv)))
 
 
 def test_naive_join_matches_oracle():
