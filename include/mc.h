@@ -124,6 +124,18 @@ int mc_update_weights(mc_job *job);
 int mc_get_weights(mc_job *job, double *out, int n);
 int mc_set_weights(mc_job *job, const double *w, int n);
 
+/* Checkpoint / resume (no counterpart in the paper).  mc_save writes the
+ * job's whole resumable state -- L, n_chains, seed, start, join order,
+ * attempts per chain, rounds joined, the carry, the bit-packed spins, W,
+ * the current iteration's histogram h and the visited mask -- to a file
+ * (MC_ESTATE while a round is pending; MC_EINVAL if the file cannot be
+ * written).  mc_load creates a new job on the current device from such a
+ * file (MC_EINVAL for a missing, foreign or truncated file, before any CUDA
+ * call); continuing it gives exactly the results the saved job would have
+ * given.  Launch shapes and traces are not saved.  Both synchronise. */
+int mc_save(mc_job *job, const char *path);
+int mc_load(const char *path, mc_job **out);
+
 /* Order of the chains at the joint (Sec. 2 steps 3-5).  mode 0 (default):
  * chain index.  mode 1: energy-ordered joining, which the end of Sec. 2
  * proposes to raise the acceptance at the joints and leaves unspecified --

@@ -20,7 +20,7 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_join_naive", "mc_histogram", "mc_update_weights", "mc_get_weights", "mc_set_weights",
     "mc_get_table", "mc_get_spins", "mc_set_spins", "mc_get_energies", "mc_get_trace",
     "mc_get_trace_chain", "mc_get_visited", "mc_set_visited", "mc_thermo", "mc_set_join_order",
-    "mc_get_order",
+    "mc_get_order", "mc_save", "mc_load",
     "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error",
     "mc_generate_noalloc", "mc_autotune", "mc_batch_run",
     "mc_job_device_bytes", "mc_server_create", "mc_server_submit", "mc_server_poll", "mc_server_wait",
@@ -116,6 +116,8 @@ def lib():
             "mc_set_visited": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
             "mc_thermo": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
             "mc_set_join_order": (ctypes.c_int, [_vp, ctypes.c_int]),
+            "mc_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+            "mc_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
             "mc_get_order": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
             "mc_get_join": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
             "mc_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(mc_info)]),
@@ -258,6 +260,16 @@ def mc_get_visited(job, out: np.ndarray):
 def mc_set_visited(job, v: np.ndarray):
     v = np.ascontiguousarray(v, dtype=np.uint8)
     _check(lib().mc_set_visited(job, _ptr(v), v.size))
+
+
+def mc_save(job, path: str):
+    _check(lib().mc_save(job, os.fsencode(path)))
+
+
+def mc_load(path: str):
+    h = _vp()
+    _check(lib().mc_load(os.fsencode(path), ctypes.byref(h)))
+    return h
 
 
 def mc_set_join_order(job, mode: int):
@@ -423,6 +435,21 @@ class Job:
     @visited.setter
     def visited(self, v):
         mc_set_visited(self.h, v)
+
+    def save(self, path: str):
+        mc_save(self.h, path)
+
+    @classmethod
+    def load(cls, path: str) -> "Job":
+        h = mc_load(path)
+        job = cls.__new__(cls)
+        job.h = h
+        info = mc_info()
+        _check(lib().mc_get_info(h, ctypes.byref(info)))
+        job.L, job.p, job.seed = info.L, info.n_chains, info.seed
+        job.N = job.L * job.L
+        job.wd = (job.L + 31) // 32
+        return job
 
     def set_join_order(self, mode: int):
         mc_set_join_order(self.h, mode)

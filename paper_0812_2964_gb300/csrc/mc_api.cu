@@ -563,6 +563,110 @@ int mc_set_visited(mc_job* job, const uint8_t* in, int n) {
   return sync(job, "visited");
 }
 
+// ------------------------------------------------------------------ save / load
+// File: "MCJOB01" + NUL, then int32 L, n_chains, start, join order; uint64
+// seed, attempts per chain; uint32 rounds joined; int32 carry valid, carry
+// level; int64 samples joined so far; then the bit-packed spins (u32), W
+// (f64), h (i64) and the visited mask (u8), all little-endian as in memory.
+namespace {
+constexpr char kMagic[8] = {'M', 'C', 'J', 'O', 'B', '0', '1', '\0'};
+
+struct FileHeader {
+  char magic[8];
+  int32_t L, p, start, order;
+  uint64_t seed, t;
+  uint32_t r;
+  int32_t carry_valid, carry;
+  int64_t joined_total;
+};
+}  // namespace
+
+int mc_save(mc_job* job, const char* path) {
+  if (int rc = check_job(job)) return rc;
+  if (!path) return fail(MC_EINVAL, "path is null");
+  if (job->pending) return fail(MC_ESTATE, "round pending: join first");
+  const size_t lat = static_cast<size_t>(job->p) * job->L * job->wd, np1 = static_cast<size_t>(job->N) + 1;
+  std::vector<uint32_t> spins(lat);
+  std::vector<double> W(np1);
+  std::vector<long long> h(np1);
+  std::vector<uint8_t> vis(np1);
+  long long st[mcgpu::kStatCount];
+  MC_CUDA(cudaMemcpyAsync(spins.data(), job->d.spins, lat * 4, cudaMemcpyDeviceToHost, job->stream), "save");
+  MC_CUDA(cudaMemcpyAsync(W.data(), job->d.W, np1 * 8, cudaMemcpyDeviceToHost, job->stream), "save");
+  MC_CUDA(cudaMemcpyAsync(h.data(), job->d.h, np1 * 8, cudaMemcpyDeviceToHost, job->stream), "save");
+  MC_CUDA(cudaMemcpyAsync(vis.data(), job->d.visited, np1, cudaMemcpyDeviceToHost, job->stream), "save");
+  MC_CUDA(cudaMemcpyAsync(st, job->d.stats, sizeof st, cudaMemcpyDeviceToHost, job->stream), "save");
+  if (int rc = sync(job, "save")) return rc;
+  FileHeader hd;
+  std::memcpy(hd.magic, kMagic, 8);
+  hd.L = job->L;
+  hd.p = job->p;
+  hd.start = job->start;
+  hd.order = job->d.ordered;
+  hd.seed = job->seed;
+  hd.t = job->t;
+  hd.r = job->r;
+  hd.carry_valid = static_cast<int32_t>(st[mcgpu::kStatCarryValid]);
+  hd.carry = static_cast<int32_t>(st[mcgpu::kStatCarry]);
+  hd.joined_total = st[mcgpu::kStatJoinedTotal];
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(MC_EINVAL, "cannot open %s for writing", path);
+  bool ok = std::fwrite(&hd, sizeof hd, 1, f) == 1 && std::fwrite(spins.data(), 4, lat, f) == lat &&
+            std::fwrite(W.data(), 8, np1, f) == np1 && std::fwrite(h.data(), 8, np1, f) == np1 &&
+            std::fwrite(vis.data(), 1, np1, f) == np1;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? MC_OK : fail(MC_EINVAL, "write to %s failed", path);
+}
+
+int mc_load(const char* path, mc_job** out) {
+  if (!out) return fail(MC_EINVAL, "out is null");
+  *out = nullptr;
+  if (!path) return fail(MC_EINVAL, "path is null");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(MC_EINVAL, "cannot open %s", path);
+  FileHeader hd;
+  if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, kMagic, 8) != 0 || hd.L < 4 || hd.L > 128 ||
+      hd.L % 4 != 0 || hd.p < 1 || hd.p > (1 << 24) || (hd.order != 0 && hd.order != 1)) {
+    std::fclose(f);
+    return fail(MC_EINVAL, "%s is not a saved job", path);
+  }
+  const int wd = (hd.L + 31) / 32;
+  const size_t lat = static_cast<size_t>(hd.p) * hd.L * wd, np1 = static_cast<size_t>(hd.L) * hd.L + 1;
+  std::vector<uint32_t> spins(lat);
+  std::vector<double> W(np1);
+  std::vector<long long> h(np1);
+  std::vector<uint8_t> vis(np1);
+  const bool ok = std::fread(spins.data(), 4, lat, f) == lat && std::fread(W.data(), 8, np1, f) == np1 &&
+                  std::fread(h.data(), 8, np1, f) == np1 && std::fread(vis.data(), 1, np1, f) == np1;
+  std::fclose(f);
+  if (!ok) return fail(MC_EINVAL, "%s is truncated", path);
+  mc_job* j = nullptr;
+  int rc = mc_init(hd.L, hd.p, hd.seed, hd.start, &j);
+  if (rc) return rc;
+  rc = mc_set_spins(j, spins.data(), lat);
+  if (!rc) rc = mc_set_weights(j, W.data(), static_cast<int>(np1));
+  if (!rc) rc = mc_set_visited(j, vis.data(), static_cast<int>(np1));
+  if (!rc) {
+    long long st[mcgpu::kStatCount] = {};
+    st[mcgpu::kStatCarryValid] = hd.carry_valid;
+    st[mcgpu::kStatCarry] = hd.carry;
+    st[mcgpu::kStatJoinedTotal] = hd.joined_total;
+    cudaError_t e = cudaMemcpyAsync(j->d.h, h.data(), np1 * 8, cudaMemcpyHostToDevice, j->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(j->d.stats, st, sizeof st, cudaMemcpyHostToDevice, j->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(j->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "load");
+  }
+  if (rc) {
+    mc_free(j);
+    return rc;
+  }
+  j->t = hd.t;
+  j->r = hd.r;
+  j->d.ordered = hd.order;
+  *out = j;
+  return MC_OK;
+}
+
 int mc_set_join_order(mc_job* job, int mode) {
   if (int rc = check_job(job)) return rc;
   if (mode != 0 && mode != 1) return fail(MC_EINVAL, "join order %d: 0 chain index, 1 ascending final energy", mode);

@@ -64,3 +64,15 @@ def test_job_device_bytes_is_a_host_query(libpath):
     assert a > 0
     assert mc.mc_job_device_bytes(32, 200, 10) > a      # more chains, more memory
     assert mc.mc_job_device_bytes(64, 100, 10) > a      # larger lattice, more memory
+
+
+def test_load_rejects_missing_and_foreign_files(libpath, tmp_path):
+    # checked before any CUDA call
+    with pytest.raises(mc.McError) as e:
+        mc.mc_load(str(tmp_path / "missing.job"))
+    assert e.value.code == mc.MC_EINVAL
+    bad = tmp_path / "foreign.job"
+    bad.write_bytes(b"not a saved job at all" * 4)
+    with pytest.raises(mc.McError) as e:
+        mc.mc_load(str(bad))
+    assert e.value.code == mc.MC_EINVAL
