@@ -656,7 +656,10 @@ template <class F, bool TS>
 inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S, uint32_t r,
                                  cudaStream_t st) {
   const size_t bytes = plan_bytes(j.L, s, TS, false);
-  const size_t pbytes = plan_bytes(j.L, s, TS, true);
+  // the prefix pass keeps a histogram beside the lattices: fewer chains a warp if need be
+  LaunchShape sp = s;
+  while (sp.cpw > 1 && plan_bytes(j.L, sp, TS, true) > kMaxSmem) --sp.cpw;
+  const size_t pbytes = plan_bytes(j.L, sp, TS, true);
   const int per_block = s.cpw * s.wpb;
   const long long items = static_cast<long long>(j.p) * j.ck_K;
   cudaError_t e = join_prelude(j, st);
@@ -733,8 +736,8 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
   if ((e = join_prefix_list(j, st)) != cudaSuccess) return e;
   if ((e = join_reset_queue(j, st)) != cudaSuccess) return e;
   const unsigned grid_pre = static_cast<unsigned>(
-      std::min<long long>(blocks_for(items, per_block), resident_blocks(kp, 32 * s.wpb, pbytes)));
-  kp<<<grid_pre, 32 * s.wpb, pbytes, st>>>(j, s.cpw, t0, S);
+      std::min<long long>(blocks_for(items, sp.cpw * sp.wpb), resident_blocks(kp, 32 * sp.wpb, pbytes)));
+  kp<<<grid_pre, 32 * sp.wpb, pbytes, st>>>(j, sp.cpw, t0, S);
   launches_add(2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return join_finalize(j, S, st);

@@ -562,18 +562,36 @@ LaunchShape dense_shape(int L, int p, int num_sms) {
   return def;
 }
 
-// The joint's replay kernels use full warps whatever shape generation runs
-// with (their work items are (chain, segment) pairs, not chains): 32 items a
-// warp, as many warps a block as fit, preferring a shape whose threshold
-// table and histogram still fit in shared memory.
+// The joint's replay kernels take their own launch shape (their work items
+// are (chain, segment) pairs, not chains): as many lanes a block as the
+// lattices leave room for, preferring shapes whose threshold table (and the
+// prefix pass's histogram) still fit in shared memory.  The prefix pass, which
+// also needs the histogram there, narrows the warps further if it must
+// (launch_join_t).  L = 128: 28 lanes x 4 warps instead of 32 x 2 -- the
+// lattices, 2 KB a lane, fill shared memory either way, and four warps keep
+// all four sub-partitions issuing.
+static bool replay_fits(int L, const LaunchShape& s) {
+  if (s.cpw < 1 || s.cpw > 32 || s.wpb < 1 || s.wpb > 4) return false;
+  if (s.placement == kPlaceReg && L > 32) return false;
+  return plan_bytes(L, s, false, false) <= kMaxSmem;
+}
+
 static LaunchShape join_shape(int L, const LaunchShape& gen) {
   LaunchShape best = gen;
-  bool have = false;
-  for (int w = 4; w >= 1; w >>= 1) {
-    LaunchShape s{gen.placement, 32, w};
-    if (!shape_supported(L, s)) continue;
-    if (table_fits(L, s, true)) return s;
-    if (!have) best = s, have = true;
+  int best_lanes = 0;
+  bool best_ts = false;
+  for (int w = 4; w >= 1; --w) {
+    int cpw = 32;
+    while (cpw > 1 && !replay_fits(L, LaunchShape{gen.placement, cpw, w})) --cpw;
+    const LaunchShape s{gen.placement, cpw, w};
+    if (!replay_fits(L, s)) continue;
+    int c2 = cpw;  // most chains per warp that leave the table and histogram in shared memory
+    while (c2 >= 1 && !table_fits(L, LaunchShape{gen.placement, c2, w}, true)) --c2;
+    if (c2 >= 16) {
+      if (!best_ts || c2 * w > best_lanes) best = LaunchShape{gen.placement, c2, w}, best_lanes = c2 * w, best_ts = true;
+    } else if (!best_ts && cpw * w > best_lanes) {
+      best = s, best_lanes = cpw * w;
+    }
   }
   return best;
 }
