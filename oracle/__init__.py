@@ -85,6 +85,8 @@ def _declare(L):
         "or_join_naive": (c.c_int64, [c.c_void_p]),
         "or_update_weights": (None, [c.c_void_p]),
         "or_iteration": (c.c_int64, [c.c_void_p, c.c_int64, c.c_int64, c.c_int]),
+        "or_iteration_adaptive": (c.c_int64, [c.c_void_p, c.c_int64, c.c_int64, c.c_int, c.c_int,
+                                              c.POINTER(c.c_int), _i64p]),
         "or_get_weights": (None, [c.c_void_p, _dp]),
         "or_set_weights": (None, [c.c_void_p, _dp]),
         "or_get_table": (None, [c.c_void_p, _u32p]),
@@ -239,6 +241,14 @@ class Job:
 
     def iteration(self, S: int, M_total: int = 0, nthreads: int = 1) -> int:
         return int(lib().or_iteration(self._h, S, M_total, nthreads))
+
+    def iteration_adaptive(self, S: int, M_total: int, nthreads: int = 1, max_rounds: int = 1000):
+        """Returns (joined, [sweeps of each round])."""
+        rounds = ctypes.c_int(0)
+        sw = np.zeros(max_rounds, dtype=np.int64)
+        joined = int(lib().or_iteration_adaptive(self._h, S, M_total, nthreads, max_rounds,
+                                                   ctypes.byref(rounds), _p(sw, _i64p)))
+        return joined, [int(x) for x in sw[:rounds.value]]
 
     @property
     def weights(self):

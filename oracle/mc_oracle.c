@@ -530,6 +530,38 @@ int64_t or_iteration(or_job *j, int64_t S, int64_t M_total, int nthreads)
     return total;
 }
 
+/* Step 6 with "M_node adjusted appropriately": after a round that leaves h
+ * short of M_total, the next round's sweeps are those that the last round's
+ * rate of kept samples per sweep needs for the remainder,
+ *   S_next = ceil(remaining * S_last / joined_last), within [1, S],
+ * and S when the last round kept nothing.  rounds_out (may be NULL) gets the
+ * number of rounds; sweeps_out (may be NULL, room for max_rounds) their S. */
+int64_t or_iteration_adaptive(or_job *j, int64_t S, int64_t M_total, int nthreads, int max_rounds,
+                              int *rounds_out, int64_t *sweeps_out)
+{
+    int64_t total = 0, s_cur = S;
+    int rounds = 0;
+    for (;;) {
+        if (or_run_round(j, s_cur, nthreads) != 0) return -1;
+        const int64_t got = or_join(j);
+        total += got;
+        if (sweeps_out && rounds < max_rounds) sweeps_out[rounds] = s_cur;
+        ++rounds;
+        if (total >= M_total || rounds >= max_rounds) break;
+        const int64_t remaining = M_total - total;
+        int64_t nxt = S;
+        if (got > 0) {
+            nxt = (remaining * s_cur + got - 1) / got;
+            if (nxt < 1) nxt = 1;
+            if (nxt > S) nxt = S;
+        }
+        s_cur = nxt;
+    }
+    or_update_weights(j);
+    if (rounds_out) *rounds_out = rounds;
+    return total;
+}
+
 int or_get_L(const or_job *j) { return j->L; }
 int or_get_p(const or_job *j) { return j->p; }
 void or_get_weights(const or_job *j, double *W) { memcpy(W, j->W, sizeof(double) * ((size_t)j->N + 1)); }

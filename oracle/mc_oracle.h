@@ -71,6 +71,9 @@ void    or_set_join_order(or_job *j, int mode);
 void    or_get_order(const or_job *j, int32_t *order);   /* [p] chain at each position */
 void    or_update_weights(or_job *j);
 int64_t or_iteration(or_job *j, int64_t S, int64_t M_total, int nthreads);
+/* rounds with adjusted sweeps until h holds M_total samples (or max_rounds) */
+int64_t or_iteration_adaptive(or_job *j, int64_t S, int64_t M_total, int nthreads, int max_rounds,
+                              int *rounds_out, int64_t *sweeps_out);
 
 int     or_get_L(const or_job *j);
 int     or_get_p(const or_job *j);

@@ -246,3 +246,33 @@ def test_energy_order_ties_and_invariants():
         if kept_in_order:
             assert o.carry == last[kept_in_order[-1]]
         o.update_weights()
+
+
+def test_adaptive_rounds_follow_the_rule():
+    # W = 0: every sample is kept, so round sizes follow from the rule by hand
+    L, p, S = 4, 6, 10
+    N = L * L
+    o = oracle.Job(L, p, 3, 1)
+    per_round = p * S * N
+    joined, sweeps = o.iteration_adaptive(S, int(2.5 * per_round), 2)
+    assert sweeps == [S, S, 5]                 # remaining 0.5 p S N at rate p N per sweep
+    assert joined == 2 * per_round + p * 5 * N
+    # the rule clamps to [1, S]: a tiny remainder still takes one sweep
+    o2 = oracle.Job(L, p, 3, 1)
+    joined2, sweeps2 = o2.iteration_adaptive(S, per_round + 1, 2)
+    assert sweeps2 == [S, 1] and joined2 == per_round + p * N
+    # an M_total already met after one round: one round
+    o3 = oracle.Job(L, p, 3, 1)
+    assert o3.iteration_adaptive(S, 1, 2)[1] == [S]
+
+
+def test_adaptive_iteration_invariants_under_rejections():
+    L, p, S = 6, 10, 4
+    N = L * L
+    o = oracle.Job(L, p, 8, 1)
+    o.weights = np.random.default_rng(2).normal(0, 6.0, N + 1)
+    M_total = 3 * p * S * N // 2
+    joined, sweeps = o.iteration_adaptive(S, M_total, 4, max_rounds=200)
+    assert joined >= M_total or len(sweeps) == 200
+    assert all(1 <= s <= S for s in sweeps) and sweeps[0] == S
+    assert o.round == len(sweeps)
