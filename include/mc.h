@@ -119,6 +119,17 @@ int mc_histogram(mc_job *job, int64_t *out, int n_bins);
  * table is rebuilt.  MC_ESTATE while a round is pending.  Asynchronous. */
 int mc_update_weights(mc_job *job);
 
+/* One weight iteration (Sec. 2 step 6, then Sec. 3.1): rounds of n_sweeps
+ * sweeps, each joined, until the iteration's histogram holds m_total
+ * samples (at least one round; at most max_rounds), then mc_update_weights.
+ * adapt != 0 adjusts M_node as step 6 allows: after a round that leaves h
+ * short, the next round has ceil(remaining * S_last / joined_last) sweeps,
+ * clamped to [1, n_sweeps] (n_sweeps if the last round kept nothing).
+ * *joined (may be NULL) = samples kept, *rounds (may be NULL) = rounds run.
+ * Synchronises after every round (the loop needs each joined length). */
+int mc_iteration(mc_job *job, int64_t n_sweeps, int64_t m_total, int adapt, int max_rounds,
+                 int64_t *joined, int *rounds);
+
 /* W = ln w (double, n = N + 1).  mc_set_weights rebuilds the thresholds;
  * MC_ESTATE while a round is pending.  mc_get_weights synchronises. */
 int mc_get_weights(mc_job *job, double *out, int n);

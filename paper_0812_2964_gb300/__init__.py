@@ -20,7 +20,7 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_join_naive", "mc_histogram", "mc_update_weights", "mc_get_weights", "mc_set_weights",
     "mc_get_table", "mc_get_spins", "mc_set_spins", "mc_get_energies", "mc_get_trace",
     "mc_get_trace_chain", "mc_get_visited", "mc_set_visited", "mc_thermo", "mc_set_join_order",
-    "mc_get_order", "mc_save", "mc_load",
+    "mc_get_order", "mc_save", "mc_load", "mc_iteration",
     "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error",
     "mc_generate_noalloc", "mc_autotune", "mc_batch_run",
     "mc_job_device_bytes", "mc_server_create", "mc_server_submit", "mc_server_poll", "mc_server_wait",
@@ -117,6 +117,8 @@ def lib():
             "mc_thermo": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
             "mc_set_join_order": (ctypes.c_int, [_vp, ctypes.c_int]),
             "mc_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+            "mc_iteration": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                            _i64p, ctypes.POINTER(ctypes.c_int)]),
             "mc_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
             "mc_get_order": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
             "mc_get_join": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
@@ -262,6 +264,15 @@ def mc_set_visited(job, v: np.ndarray):
     _check(lib().mc_set_visited(job, _ptr(v), v.size))
 
 
+def mc_iteration(job, n_sweeps: int, m_total: int = 0, adapt: bool = False, max_rounds: int = 1_000_000):
+    """One weight iteration; returns (joined, rounds)."""
+    joined = ctypes.c_int64(0)
+    rounds = ctypes.c_int(0)
+    _check(lib().mc_iteration(job, n_sweeps, m_total, 1 if adapt else 0, max_rounds, ctypes.byref(joined),
+                              ctypes.byref(rounds)))
+    return joined.value, rounds.value
+
+
 def mc_save(job, path: str):
     _check(lib().mc_save(job, os.fsencode(path)))
 
@@ -382,16 +393,6 @@ class Job:
     def update_weights(self):
         mc_update_weights(self.h)
 
-    def iteration(self, S: int, M_total: int = 0) -> int:
-        total = 0
-        while True:
-            self.run_sweeps(S)
-            total += self.join()
-            if total >= M_total:
-                break
-        self.update_weights()
-        return total
-
     @property
     def hist(self):
         return mc_histogram(self.h, np.zeros(self.N + 1, np.int64))
@@ -435,6 +436,9 @@ class Job:
     @visited.setter
     def visited(self, v):
         mc_set_visited(self.h, v)
+
+    def iteration(self, n_sweeps: int, m_total: int = 0, adapt: bool = False, max_rounds: int = 1_000_000):
+        return mc_iteration(self.h, n_sweeps, m_total, adapt, max_rounds)
 
     def save(self, path: str):
         mc_save(self.h, path)

@@ -403,6 +403,38 @@ int mc_histogram(mc_job* job, int64_t* out, int n_bins) {
   return sync(job, "histogram");
 }
 
+// Step 6 of Sec. 2 and the update of Sec. 3.1 in one call: rounds of
+// n_sweeps until h holds m_total samples (at least one round), then the
+// weight update.  adapt != 0: after a short round the next one has
+// ceil(remaining * S_last / joined_last) sweeps, within [1, n_sweeps]
+// (n_sweeps when the last round kept nothing).
+int mc_iteration(mc_job* job, int64_t n_sweeps, int64_t m_total, int adapt, int max_rounds, int64_t* joined,
+                 int* rounds) {
+  if (int rc = check_job(job)) return rc;
+  if (job->pending) return fail(MC_ESTATE, "round pending: join first");
+  if (n_sweeps < 1 || m_total < 0 || max_rounds < 1) return fail(MC_EINVAL, "need n_sweeps >= 1, m_total >= 0, max_rounds >= 1");
+  int64_t total = 0, s_cur = n_sweeps;
+  int r = 0;
+  for (;;) {
+    if (int rc = mc_run_sweeps(job, s_cur)) return rc;
+    int64_t got = 0;
+    if (int rc = mc_join(job, &got)) return rc;
+    total += got;
+    ++r;
+    if (total >= m_total || r >= max_rounds) break;
+    int64_t nxt = n_sweeps;
+    if (adapt && got > 0) {
+      nxt = ((m_total - total) * s_cur + got - 1) / got;
+      nxt = std::max<int64_t>(1, std::min<int64_t>(nxt, n_sweeps));
+    }
+    s_cur = nxt;
+  }
+  if (int rc = mc_update_weights(job)) return rc;
+  if (joined) *joined = total;
+  if (rounds) *rounds = r;
+  return MC_OK;
+}
+
 int mc_update_weights(mc_job* job) {
   if (int rc = check_job(job)) return rc;
   if (job->pending) return fail(MC_ESTATE, "round pending: join first");

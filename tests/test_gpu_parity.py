@@ -210,3 +210,25 @@ def test_autotune_picks_a_supported_shape_and_keeps_results():
     assert g.join() == o.join()
     assert np.array_equal(g.hist, o.hist)
     assert mc.mc_autotune(g.h, 2, True) == shape   # cached
+
+
+@pytest.mark.parametrize("L,p,S,adapt", [(8, 30, 4, True), (16, 50, 3, True), (32, 40, 2, False)])
+def test_iteration_with_m_total_matches_oracle(L, p, S, adapt):
+    # step 6: rounds until h holds M_total samples, adaptive round lengths
+    N = L * L
+    W = random_weights(L, seed=L + 1, scale=6.0)
+    g = mc.Job(L, p, 700 + L, 1)
+    o = oracle.Job(L, p, 700 + L, 1)
+    g.weights = W
+    o.weights = W
+    M_total = 5 * p * S * N // 2
+    for _ in range(3):
+        jg, rg = g.iteration(S, M_total, adapt=adapt, max_rounds=50)
+        if adapt:
+            jo, sweeps = o.iteration_adaptive(S, M_total, 8, max_rounds=50)
+            assert rg == len(sweeps)
+        else:
+            jo = o.iteration(S, M_total, 8)
+        assert jg == jo
+        _compare_state(g, o, L)
+        _compare_weights(g, o)
