@@ -155,10 +155,6 @@ __device__ __forceinline__ BlockCtx block_setup(const DevJob& j, const SmemPlan&
 }
 
 // ------------------------------------------------------------------ generation
-struct NoSweepHook {
-  __device__ __forceinline__ void operator()(int64_t, int) const {}
-};
-
 template <int L>
 struct RunnerFactoryReg {
   __device__ __forceinline__ static RegRunner<L> make(const BlockCtx&, int) { return RegRunner<L>(); }
