@@ -190,7 +190,10 @@ __device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const u
   __syncthreads();
   int m = 0;
   Prefetch pf;
-  GenHook hk{b.hist, b.owner ? 1u : 0u};
+  // (one lane a chain: every lane counts; a compile-time 1 keeps the
+  // reduction's operand an immediate)
+  GenHook hk{b.hist, GL == 1 ? 1u : (b.owner ? 1u : 0u)};
+  const bool writer = GL == 1 ? b.active : b.owner;
   if (b.active) {
     run.load(j.spins + static_cast<size_t>(b.chain) * j.L * j.wd);
     m = j.m[b.chain];
@@ -199,10 +202,11 @@ __device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const u
   const size_t lw = static_cast<size_t>(j.L) * j.wd;
   // the lanes of the warp's working lane groups: they meet again after every
   // write that only a group's first lane makes, before the next shuffles
-  const unsigned amask = __ballot_sync(0xFFFFFFFFu, b.active);
+  unsigned amask = 0xFFFFFFFFu;
+  if constexpr (GL > 1) amask = __ballot_sync(0xFFFFFFFFu, b.active);
   for (int64_t s = 0; s < S; ++s) {
     if (b.active) {
-      if (j.ckpt && (s % j.ck_C) == 0 && b.owner) {
+      if (j.ckpt && (s % j.ck_C) == 0 && writer) {
         // lattice and level at the start of segment s / C, for the joint's replays
         const size_t seg = static_cast<size_t>(s / j.ck_C);
         run.save_strided(j.ckpt + seg * lw * j.p + b.chain, static_cast<size_t>(j.p));
@@ -210,7 +214,7 @@ __device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const u
       }
       if constexpr (GL > 1) __syncwarp(amask);
       run.template sweep<false, GL>(m, pf, b.T, j.np1, static_cast<uint32_t>(b.chain), j.key0, j.key1, hk);
-      if (do_trace && b.owner) j.trace[s * j.p + b.chain] = 4 * m - 2 * j.N;
+      if (do_trace && writer) j.trace[s * j.p + b.chain] = 4 * m - 2 * j.N;
       if constexpr (GL > 1) __syncwarp(amask);
     }
     if (flushF > 0 && (s + 1) % flushF == 0 && s + 1 < S) {
@@ -227,7 +231,7 @@ __device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const u
       __syncthreads();
     }
   }
-  if (b.owner) {
+  if (writer) {
     hk.flush(m);
     run.store(j.spins + static_cast<size_t>(b.chain) * j.L * j.wd);
     j.m[b.chain] = m;
