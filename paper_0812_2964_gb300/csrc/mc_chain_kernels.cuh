@@ -637,6 +637,7 @@ inline cudaError_t launch_gen_t(const DevJob& j, const LaunchShape& s, uint64_t 
                                 cudaStream_t st) {
   const size_t bytes = plan_bytes(j.L, s, TS, true);
   // lattice in shared memory with at most 8 chains a warp: lane groups of 4
+  // (groups of 8 for at most 4 chains measured slower at L = 48, 64 and 128)
   auto kern = gen_kernel<F, TS, 1>;
   if constexpr (F::kPlacement == kPlaceSmem)
     if (s.cpw <= 8) kern = gen_kernel<F, TS, 4>;

@@ -232,3 +232,31 @@ def test_iteration_with_m_total_matches_oracle(L, p, S, adapt):
         assert jg == jo
         _compare_state(g, o, L)
         _compare_weights(g, o)
+
+
+@pytest.mark.parametrize("L,start", [(4, 0), (12, 1), (64, 1)])
+def test_single_chain(L, start):
+    # p = 1: the joint has one chain; after the first round it checks against
+    # its own last level of the previous round
+    _run_parity(L, 1, 3, 3, start, seed=60 + L, weights=random_weights(L, L, 5.0))
+
+
+def test_first_iteration_closed_form_on_the_gpu():
+    # W = 0: every flip is accepted, so one sweep flips every spin in order and
+    # returns to the starting energy; every chain is kept whole (k = 1)
+    L, p, S = 8, 37, 3
+    N = L * L
+    g = mc.Job(L, p, 3, 0)                      # all up: E = -2N
+    g.set_trace(True)
+    g.run_sweeps(S)
+    assert (g.trace == -2 * N).all()
+    assert g.join() == p * S * N
+    assert (g.k == 1).all()
+    assert g.hist.sum() == p * S * N
+
+
+def test_round_length_limit():
+    g = mc.Job(128, 2, 1, 1)
+    with pytest.raises(mc.McError) as e:
+        mc.mc_run_sweeps(g.h, (1 << 34) // (128 * 128))    # M = S N would reach 2^34
+    assert e.value.code == mc.MC_EINVAL
