@@ -45,7 +45,7 @@ extern "C" {
 #define MC_ENOMEM (-2)   /* device or host allocation failed */
 #define MC_ECUDA (-3)    /* a CUDA call failed (message has the CUDA error) */
 #define MC_ESTATE (-4)   /* call out of order (e.g. mc_join without a round) */
-#define MC_ETIMEOUT (-5) /* a bounded device wait gave up */
+#define MC_ETIMEOUT (-5) /* reserved: no call waits on the device without a bound */
 
 typedef struct mc_job mc_job;
 
@@ -96,13 +96,17 @@ int mc_set_trace(mc_job *job, int enabled);
  * n_sweeps >= 1 and n_sweeps * N < 2^34. */
 int mc_run_sweeps(mc_job *job, int64_t n_sweeps);
 
-/* Sec. 2 steps 3-5 for the last round: chain i (in order) keeps its samples
- * from the first one that passes the Metropolis test against the energy
- * passed on by the chains before it (chain 0: by the previous round; in the
- * job's first round chain 0 is kept whole); a chain with no such sample
- * keeps nothing and passes on what it received.  Kept samples are added to
- * h.  If joined_len is not NULL the call synchronises and stores the number
- * of samples kept in this round.  MC_ESTATE without a pending round. */
+/* Sec. 2 steps 3-5 for the last round: chain i (in order; see
+ * mc_set_join_order) keeps its samples from the first one that passes the
+ * Metropolis test against the energy passed on by the chains before it
+ * (chain 0: by the previous round; in the job's first round chain 0 is kept
+ * whole); a chain with no such sample keeps nothing and passes on what it
+ * received.  Kept samples are added to h.  The serial rule is evaluated in
+ * parallel: speculative searches from lattice checkpoints, resolution
+ * passes, an exact scan over per-level summaries when speculation does not
+ * settle; the result is that of the serial rule.  Asynchronous; if
+ * joined_len is not NULL the call synchronises and stores the number of
+ * samples kept in this round.  MC_ESTATE without a pending round. */
 int mc_join(mc_job *job, int64_t *joined_len);
 
 /* The control of Sec. 5 / Fig. 2: concatenate the last round's chains whole,
