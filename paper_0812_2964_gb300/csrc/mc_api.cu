@@ -468,13 +468,16 @@ int mc_batch_run(mc_job** jobs, int n_jobs, int iterations, int64_t n_sweeps, in
     saved[i] = jobs[i]->stream;
     jobs[i]->stream = st;
   }
-  // shapes for the fused launch: full warps (as many chains per warp as fit
-  // beside the threshold table).  A round takes as long as its slowest
-  // chain either way, and full warps let every job's blocks be resident at
-  // once, so the fused round lasts as long as the longest job's, not the sum.
+  // shapes for the fused launch.  A round takes as long as its slowest chain,
+  // so the blocks of all jobs should be resident at once: few warps per job,
+  // the longest chains first (below).
   std::vector<LaunchShape> bshape(n_jobs);
   std::vector<char> fused(n_jobs, 0);
   for (int i = 0; i < n_jobs && mode > 0; ++i) {
+    // full warps.  (Lane groups for the shared-memory jobs -- 8 chains a
+    // warp, 4 lanes each -- shorten their chains' critical path but need
+    // four times the blocks, which then no longer all fit at once: measured
+    // 1.04e11 against 1.10e11 kept attempts/s on the uneven batch.)
     LaunchShape s{jobs[i]->L <= 32 ? mcgpu::kPlaceReg : mcgpu::kPlaceSmem, std::min(32, jobs[i]->p),
                   mcgpu::kBatchWarps};
     while (s.cpw > 1 && !mcgpu::batch_supported(jobs[i]->L, s)) s.cpw >>= 1;

@@ -19,8 +19,14 @@ __global__ void __launch_bounds__(128) gen_batched_kernel(const BatchParams P) {
     case 16: gen_body<RegF<16>, true>(it.j, it.cpw, it.t0, it.S, it.flushF, it.trace, block); break;
     case 24: gen_body<RegF<24>, true>(it.j, it.cpw, it.t0, it.S, it.flushF, it.trace, block); break;
     case 32: gen_body<RegF<32>, true>(it.j, it.cpw, it.t0, it.S, it.flushF, it.trace, block); break;
-    case 48: gen_body<SmemF<2, 48>, true>(it.j, it.cpw, it.t0, it.S, it.flushF, it.trace, block); break;
-    case 64: gen_body<SmemF<2, 64>, true>(it.j, it.cpw, it.t0, it.S, it.flushF, it.trace, block); break;
+    case 48:
+      if (it.gl == 4) gen_body<SmemF<2, 48>, true, 4>(it.j, it.cpw, it.t0, it.S, it.flushF, it.trace, block);
+      else gen_body<SmemF<2, 48>, true>(it.j, it.cpw, it.t0, it.S, it.flushF, it.trace, block);
+      break;
+    case 64:
+      if (it.gl == 4) gen_body<SmemF<2, 64>, true, 4>(it.j, it.cpw, it.t0, it.S, it.flushF, it.trace, block);
+      else gen_body<SmemF<2, 64>, true>(it.j, it.cpw, it.t0, it.S, it.flushF, it.trace, block);
+      break;
     default: break;
   }
 }
@@ -35,6 +41,7 @@ cudaError_t batch_item(const DevJob& j, const LaunchShape& s, uint64_t t0, int64
                        size_t* smem_bytes, int* blocks) {
   out->j = j;
   out->cpw = s.cpw;
+  out->gl = (s.placement == kPlaceSmem && s.cpw <= 8) ? 4 : 1;
   out->t0 = t0;
   out->S = S;
   out->trace = trace ? 1 : 0;

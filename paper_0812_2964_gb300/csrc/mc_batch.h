@@ -10,6 +10,7 @@ constexpr int kBatchWarps = 4;  // warps per block in the fused launch
 struct BatchItem {
   DevJob j;
   int cpw;
+  int gl;           // lanes per chain (4: lane groups, lattice in shared memory and cpw <= 8)
   int first_block;  // first block of this job in the fused grid
   int trace;
   uint64_t t0;
