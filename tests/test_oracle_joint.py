@@ -276,3 +276,24 @@ def test_adaptive_iteration_invariants_under_rejections():
     assert joined >= M_total or len(sweeps) == 200
     assert all(1 <= s <= S for s in sweeps) and sweeps[0] == S
     assert o.round == len(sweeps)
+
+
+def test_acceptance_from_per_level_minimum_uniforms():
+    # The identity the GPU's exact scan relies on (Sec. 2 step 4): a chain
+    # keeps samples for input x iff some visited level m has
+    # min{u_k : m_k = m} <= thr(W[m] - W[x]).  Checked against the oracle's
+    # literal scan on random sequences, weights and inputs.
+    rng = np.random.default_rng(11)
+    N = 36
+    for trial in range(60):
+        M = int(rng.integers(8, 200))
+        lv = np.clip(np.cumsum(rng.integers(-2, 3, M)) + int(rng.integers(5, 30)), 0, N).astype(np.int32)
+        W = rng.normal(0, float(rng.choice([0.5, 3.0, 12.0])), N + 1)
+        x = int(rng.integers(0, N + 1))
+        r, i = int(rng.integers(0, 5)), int(rng.integers(0, 50))
+        umin = {}
+        for k in range(1, M + 1):
+            u = _ju(r, i, k)
+            umin[int(lv[k - 1])] = min(umin.get(int(lv[k - 1]), 0xFFFFFFFF), u)
+        accept = any(u <= oracle.threshold(W[m] - W[x]) for m, u in umin.items())
+        assert accept == (oracle.joint_scan(lv, W, x, SEED, r, i) > 0), trial
