@@ -43,7 +43,8 @@ WORKLOADS = {
     "L64_p4096": Workload("L64_p4096", 64, 4096, 200_000, 100, 3, 1),
     "L128_p1024": Workload("L128_p1024", 128, 1024, 200_000, 100, 3, 1),
     # the paper's own lattice sizes
-    "L100_p32": Workload("L100_p32", 100, 32, 1000, 1300, 9, 1, "Table 1 lattice (M_total/p per chain)"),
+    "L100_p32": Workload("L100_p32", 100, 32, 313, 1300, 9, 1,
+                         "Table 1: M_node = M_total / p = 3.125e6 samples, rounded up to whole sweeps"),
     "L20_p32": Workload("L20_p32", 20, 32, 1, 10, 10, 1, "Fig. 2 lattice"),
 }
 
