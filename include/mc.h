@@ -139,6 +139,16 @@ int mc_iteration(mc_job *job, int64_t n_sweeps, int64_t m_total, int adapt, int 
 int mc_get_weights(mc_job *job, double *out, int n);
 int mc_set_weights(mc_job *job, const double *w, int n);
 
+/* How the joint resolves wrong speculations (performance only: every
+ * policy gives the serial rule's result).  Rounds of at most
+ * scan_max_samples samples (all chains; < 0: the default 2e10) run
+ * passes_before_scan speculative passes, then the summary replay and the
+ * exact scan if chains are still pending, then passes_before_scan passes
+ * more; larger rounds run passes_without_scan passes; whatever is left goes
+ * to the one-block fallback.  Passes in 0..64 (defaults 2 and 10).
+ * MC_ESTATE while a round is pending. */
+int mc_set_join_policy(mc_job *job, int64_t scan_max_samples, int passes_before_scan, int passes_without_scan);
+
 /* Checkpoint / resume (no counterpart in the paper).  mc_save writes the
  * job's whole resumable state -- L, n_chains, seed, start, join order,
  * attempts per chain, rounds joined, the carry, the bit-packed spins, W,

@@ -20,7 +20,7 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_join_naive", "mc_histogram", "mc_update_weights", "mc_get_weights", "mc_set_weights",
     "mc_get_table", "mc_get_spins", "mc_set_spins", "mc_get_energies", "mc_get_trace",
     "mc_get_trace_chain", "mc_get_visited", "mc_set_visited", "mc_thermo", "mc_set_join_order",
-    "mc_get_order", "mc_save", "mc_load", "mc_iteration",
+    "mc_get_order", "mc_save", "mc_load", "mc_iteration", "mc_set_join_policy",
     "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error",
     "mc_generate_noalloc", "mc_autotune", "mc_batch_run",
     "mc_job_device_bytes", "mc_server_create", "mc_server_submit", "mc_server_poll", "mc_server_wait",
@@ -116,6 +116,7 @@ def lib():
             "mc_set_visited": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
             "mc_thermo": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
             "mc_set_join_order": (ctypes.c_int, [_vp, ctypes.c_int]),
+            "mc_set_join_policy": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int]),
             "mc_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
             "mc_iteration": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                             _i64p, ctypes.POINTER(ctypes.c_int)]),
@@ -281,6 +282,11 @@ def mc_load(path: str):
     h = _vp()
     _check(lib().mc_load(os.fsencode(path), ctypes.byref(h)))
     return h
+
+
+def mc_set_join_policy(job, scan_max_samples: int = -1, passes_before_scan: int = 2,
+                       passes_without_scan: int = 10):
+    _check(lib().mc_set_join_policy(job, scan_max_samples, passes_before_scan, passes_without_scan))
 
 
 def mc_set_join_order(job, mode: int):
@@ -454,6 +460,10 @@ class Job:
         job.N = job.L * job.L
         job.wd = (job.L + 31) // 32
         return job
+
+    def set_join_policy(self, scan_max_samples: int = -1, passes_before_scan: int = 2,
+                        passes_without_scan: int = 10):
+        mc_set_join_policy(self.h, scan_max_samples, passes_before_scan, passes_without_scan)
 
     def set_join_order(self, mode: int):
         mc_set_join_order(self.h, mode)

@@ -181,6 +181,9 @@ int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
   d.p = n_chains;
   d.key0 = static_cast<uint32_t>(seed);
   d.key1 = static_cast<uint32_t>(seed >> 32);
+  d.passes_scan = mcgpu::kGridPassesScan;
+  d.passes_plain = mcgpu::kGridPasses;
+  d.scan_max_samples = mcgpu::kScanMaxSamples;
   const size_t lat = static_cast<size_t>(n_chains) * L * j->wd;
   const size_t np1 = static_cast<size_t>(d.np1);
   if ((rc = dalloc(j, &d.spins, lat)) || (rc = dalloc(j, &d.spins0, lat)) || (rc = dalloc(j, &d.m, n_chains)) ||
@@ -699,6 +702,17 @@ int mc_load(const char* path, mc_job** out) {
   j->r = hd.r;
   j->d.ordered = hd.order;
   *out = j;
+  return MC_OK;
+}
+
+int mc_set_join_policy(mc_job* job, int64_t scan_max_samples, int passes_before_scan, int passes_without_scan) {
+  if (int rc = check_job(job)) return rc;
+  if (job->pending) return fail(MC_ESTATE, "round pending");
+  if (passes_before_scan < 0 || passes_before_scan > 64 || passes_without_scan < 0 || passes_without_scan > 64)
+    return fail(MC_EINVAL, "passes must be in 0..64");
+  job->d.scan_max_samples = scan_max_samples < 0 ? mcgpu::kScanMaxSamples : scan_max_samples;
+  job->d.passes_scan = passes_before_scan;
+  job->d.passes_plain = passes_without_scan;
   return MC_OK;
 }
 

@@ -700,12 +700,12 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
     }
     return cudaSuccess;
   };
-  const bool exact_scan = static_cast<long long>(j.p) * S * j.N <= kScanMaxSamples;
+  const bool exact_scan = static_cast<long long>(j.p) * S * j.N <= j.scan_max_samples;
   if (exact_scan) {
     // a few speculative passes; if chains are still pending, the summary
     // replay and the exact scan settle every input, one search finds the
     // new k's, and the ordinary passes catch what the scan left
-    if ((e = pass(kGridPassesScan)) != cudaSuccess) return e;
+    if ((e = pass(j.passes_scan)) != cudaSuccess) return e;
     if ((e = join_mark(j, st, false)) != cudaSuccess) return e;
     if ((e = join_summary_init(j, st)) != cudaSuccess) return e;
     if ((e = join_reset_queue(j, st)) != cudaSuccess) return e;
@@ -721,9 +721,9 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
     if ((e = join_tj_list(j, st)) != cudaSuccess) return e;
     if ((e = search(1)) != cudaSuccess) return e;
     if ((e = join_select(j, true, st)) != cudaSuccess) return e;
-    if ((e = pass(kGridPassesScan)) != cudaSuccess) return e;
+    if ((e = pass(j.passes_scan)) != cudaSuccess) return e;
   } else {
-    if ((e = pass(kGridPasses)) != cudaSuccess) return e;
+    if ((e = pass(j.passes_plain)) != cudaSuccess) return e;
   }
   auto kr = resolve_kernel<F, TS>;
   if ((e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=

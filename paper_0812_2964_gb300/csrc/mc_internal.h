@@ -49,6 +49,10 @@ struct DevJob {
   int32_t* perm;       // [p] chain at each position of the joint (identity unless ordered)
   int32_t* lvcnt;      // [np1] scratch of the energy ordering
   int ordered;         // 1: chains joined by ascending final level (ties by index)
+  // resolution policy of the joint (defaults kGridPassesScan, kGridPasses,
+  // kScanMaxSamples; mc_set_join_policy changes them)
+  int passes_scan, passes_plain;
+  long long scan_max_samples;
   int ck_C;            // sweeps per segment in the current round
   int ck_K;            // segments in the current round
   int kcap;            // segment capacity

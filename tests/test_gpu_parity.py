@@ -36,9 +36,11 @@ def _compare_weights(g, o):
     assert np.array_equal(g.visited, o.visited)
 
 
-def _run_parity(L, p, S, iters, start, seed, weights=None, shape=None, M_total=0, order=0):
+def _run_parity(L, p, S, iters, start, seed, weights=None, shape=None, M_total=0, order=0, policy=None):
     N = L * L
     g = mc.Job(L, p, seed, start)
+    if policy is not None:
+        g.set_join_policy(*policy)
     if shape is not None:
         g.set_launch_shape(*shape)
     g.set_trace(True)
@@ -120,6 +122,17 @@ def test_energy_ordered_joint_matches_oracle(L, p, S, scale):
     order = g.order
     lv = (g.energies.astype(np.int64) + 2 * L * L) // 4
     assert list(order) == list(np.lexsort((np.arange(p), lv)))
+
+
+@pytest.mark.parametrize("policy", [(0, 0, 0), (-1, 0, 0), (0, 0, 64), (-1, 1, 3)])
+@pytest.mark.parametrize("L,p,S", [(8, 40, 3), (32, 70, 2)])
+def test_every_resolution_path_gives_the_serial_rule(policy, L, p, S):
+    # (0,0,0): no passes, no scan -- the one-block fallback resolves all;
+    # (-1,0,0): straight to the summary replay and exact scan;
+    # (0,0,64): speculative passes only; (-1,1,3): one pass, then the scan
+    W = random_weights(L, seed=L + 9, scale=10.0)
+    g, o, mism = _run_parity(L, p, S, 3, 1, seed=900 + L, weights=W, policy=policy)
+    assert mism > 0
 
 
 def test_naive_join_matches_oracle():
