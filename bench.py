@@ -303,6 +303,9 @@ def run_gpu(args):
     tr = _traffic_record()
     traffic = tr.get("bytes_per_launch") if (tr.get("workload") == args.workload and tr.get("sweeps") == S
                                              and tr.get("kernel_rev") == mc.KERNEL_REV) else None
+    # issue-slot use of the same kernel measured by ncu (the 50 % target is on this)
+    issue = tr.get("issue_active_pct") if (tr.get("workload") == args.workload
+                                            and tr.get("kernel_rev") == mc.KERNEL_REV) else None
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -328,6 +331,8 @@ def run_gpu(args):
                      "kernel": "gen_kernel (lattice rows in %s)" % ["registers", "shared memory"][info["placement"]],
                      "kernel_ms": statistics.mean(gen_ms),
                      "ops_per_attempt": ALG_OPS_PER_ATTEMPT,
+                     "measured_issue_active": (issue / 100.0) if issue is not None else None,
+                     "measured_issue_source": tr.get("issue_active_source") if issue is not None else None,
                      "peak_source": f"{SMS} SMs x {SUBPARTITIONS} sub-partitions x {LANES} lanes x "
                                     f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"},
         "e2e": {"value": e2e_all / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
