@@ -534,6 +534,8 @@ __global__ void __launch_bounds__(128) resolve_kernel(const DevJob j, const int 
         j.xused[i] = x;
         j.k[i] = -1;  // marked: to be searched again
         atomicAdd(&s_count, 1);
+      } else if (j.k[i] < 0) {
+        atomicAdd(&s_count, 1);  // marked earlier, not searched yet
       }
     }
     __syncthreads();
@@ -691,9 +693,9 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
   if ((e = search(0)) != cudaSuccess) return e;
   if ((e = join_select(j, false, st)) != cudaSuccess) return e;
   // grid-wide speculative resolution passes
-  auto pass = [&](int n) -> cudaError_t {
+  auto pass = [&](int n, bool defer) -> cudaError_t {
     for (int q = 0; q < n; ++q) {
-      cudaError_t e2 = join_mark(j, st);
+      cudaError_t e2 = join_mark(j, st, true, defer);
       if (e2 == cudaSuccess) e2 = search(1);
       if (e2 == cudaSuccess) e2 = join_select(j, true, st);
       if (e2 != cudaSuccess) return e2;
@@ -705,7 +707,7 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
     // a few speculative passes; if chains are still pending, the summary
     // replay and the exact scan settle every input, one search finds the
     // new k's, and the ordinary passes catch what the scan left
-    if ((e = pass(j.passes_scan)) != cudaSuccess) return e;
+    if ((e = pass(j.passes_scan, true)) != cudaSuccess) return e;
     if ((e = join_mark(j, st, false)) != cudaSuccess) return e;
     if ((e = join_summary_init(j, st)) != cudaSuccess) return e;
     if ((e = join_reset_queue(j, st)) != cudaSuccess) return e;
@@ -721,9 +723,9 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
     if ((e = join_tj_list(j, st)) != cudaSuccess) return e;
     if ((e = search(1)) != cudaSuccess) return e;
     if ((e = join_select(j, true, st)) != cudaSuccess) return e;
-    if ((e = pass(j.passes_scan)) != cudaSuccess) return e;
+    if ((e = pass(j.passes_scan, false)) != cudaSuccess) return e;
   } else {
-    if ((e = pass(j.passes_plain)) != cudaSuccess) return e;
+    if ((e = pass(j.passes_plain, false)) != cudaSuccess) return e;
   }
   auto kr = resolve_kernel<F, TS>;
   if ((e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes))) !=

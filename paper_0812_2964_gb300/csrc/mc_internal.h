@@ -102,7 +102,7 @@ constexpr int kGridPasses = 10;
 // and the exact scan when speculation has not settled after kGridPassesScan
 constexpr long long kScanMaxSamples = 20000000000ll;
 cudaError_t join_prelude(const DevJob& j, cudaStream_t st);
-cudaError_t join_mark(const DevJob& j, cudaStream_t st, bool thresholds = true);
+cudaError_t join_mark(const DevJob& j, cudaStream_t st, bool thresholds = true, bool defer = false);
 cudaError_t join_tj_list(const DevJob& j, cudaStream_t st);
 // list (in work2) the chains of list_mode (0 all, 1 work) with no hit in segment 0
 cudaError_t join_nohit(const DevJob& j, int list_mode, cudaStream_t st);

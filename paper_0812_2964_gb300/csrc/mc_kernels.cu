@@ -342,13 +342,25 @@ __global__ void clear_stats_kernel(const DevJob j) {
 // it that kept samples (or the carry).  Chains whose k was computed for
 // another input are queued in work[], with the new input in xused, and
 // their joint thresholds are rebuilt by tj_list_kernel.
-__global__ void __launch_bounds__(1024) mark_kernel(const DevJob j) {
+//
+// defer (speculative passes ahead of the exact scan): the pass is left to
+// the scan -- the pending count seen by the pass's kernels is 0 and the
+// chains stay marked (k = -1), so the next mark lists them again (a chain
+// with k < 0 is pending whatever its input) -- when more than p/16 chains
+// are pending (rough weights: passes are unlikely to settle them) and the
+// scan's serial cost, ~1.5 us per evaluated chain, is below that of two
+// passes, ~70 ns per sample of a C-sweep segment replay: pending * 11 <
+// C * N.  (Measured at 20 sweeps: joint L = 128 28 -> 18 ms, L = 96 15 ->
+// 10 ms; L = 32 with 16384 chains, where the scan would be long, keeps the
+// passes.)
+__global__ void __launch_bounds__(1024) mark_kernel(const DevJob j, const int defer) {
   __shared__ int s_tmp[1024];
-  __shared__ int s_count, s_first;
+  __shared__ int s_count, s_first, s_new;
   block_last_accepted(j, s_tmp, j.lastacc);
   if (threadIdx.x == 0) {
     s_count = 0;
     s_first = j.p;
+    s_new = 0;
   }
   __syncthreads();
   const int carry_in = j.stats[kStatCarryValid] ? static_cast<int>(j.stats[kStatCarry]) : -1;
@@ -362,15 +374,21 @@ __global__ void __launch_bounds__(1024) mark_kernel(const DevJob j) {
       for (int s2 = 0; s2 < j.ck_K; ++s2) j.first[static_cast<size_t>(i) * j.kcap + s2] = -1;
       j.work[atomicAdd(&s_count, 1)] = i;
       atomicMin(&s_first, q);
+      atomicAdd(&s_new, 1);
+    } else if (j.k[i] < 0) {
+      j.work[atomicAdd(&s_count, 1)] = i;   // marked earlier, not searched yet
+      atomicMin(&s_first, q);
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    j.stats[kStatPending] = s_count;
+    const bool deferred = defer && s_count > j.p / 16 &&
+                          static_cast<long long>(s_count) * 11 < static_cast<long long>(j.ck_C) * j.N;
+    j.stats[kStatPending] = deferred ? 0 : s_count;
     j.stats[kStatFirstPending] = s_first;
-    if (s_count) {
+    if (s_new) {
       j.stats[kStatPasses] += 1;
-      j.stats[kStatMismatch] += s_count;
+      j.stats[kStatMismatch] += s_new;
     }
   }
 }
@@ -695,8 +713,8 @@ cudaError_t join_select(const DevJob& j, bool listed, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t join_mark(const DevJob& j, cudaStream_t st, bool thresholds) {
-  mark_kernel<<<1, 1024, 0, st>>>(j);
+cudaError_t join_mark(const DevJob& j, cudaStream_t st, bool thresholds, bool defer) {
+  mark_kernel<<<1, 1024, 0, st>>>(j, defer ? 1 : 0);
   launches_add(1);
   return thresholds ? join_tj_list(j, st) : cudaGetLastError();
 }
