@@ -177,3 +177,36 @@ def test_batch_uneven_fused_graph_sampled():
                 assert np.array_equal(words[c], w1)
                 assert lv[c] == m1
                 assert k[c] == kc
+
+
+@pytest.mark.parametrize("name,S,iters", [("L32_p16384", 10, 3), ("L64_p4096", 2, 3), ("L128_p1024", 1, 2)])
+def test_all_chains_bit_exact_at_full_chain_count(name, S, iters):
+    # every chain of the workload (its L, p, seed and start) against the
+    # oracle, with the sweeps per round cut so that the oracle keeps every
+    # sample of the round in memory: spins, energies, traces, k, histograms,
+    # weights.  The energies also equal a from-scratch recomputation from the
+    # GPU's own lattices (the trace's last entry is the chain's energy).
+    w = WORKLOADS[name]
+    L, p, N = w.L, w.chains, w.N
+    g = mc.Job(L, p, w.seed, w.start)
+    g.set_trace(True)
+    o = oracle.Job(L, p, w.seed, w.start)
+    threads = os.cpu_count() or 1
+    for _ in range(iters):
+        g.run_sweeps(S)
+        o.run_round(S, threads)
+        assert np.array_equal(g.spin_words, oracle.pack_spins(o.spins))
+        E = g.energies
+        assert np.array_equal(E, 4 * o.levels - 2 * N)
+        tr = g.trace
+        assert np.array_equal(tr, 4 * o.trace - 2 * N)
+        assert np.array_equal(tr[-1], E)
+        spins = oracle.unpack_spins(g.spin_words, L)
+        for c in (0, p // 2, p - 1):
+            assert oracle.energy(spins[c]) == E[c]
+        assert g.join() == o.join()
+        assert np.array_equal(g.k, o.k)
+        assert np.array_equal(g.hist, o.hist)
+        g.update_weights()
+        o.update_weights()
+        assert np.array_equal(g.weights, o.weights)
