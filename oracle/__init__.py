@@ -81,6 +81,8 @@ def _declare(L):
         "or_create": (c.c_void_p, [c.c_int, c.c_int, c.c_uint64, c.c_int]),
         "or_free": (None, [c.c_void_p]),
         "or_run_round": (c.c_int, [c.c_void_p, c.c_int64, c.c_int]),
+        "or_run_attempts": (c.c_int, [c.c_void_p, c.c_int64, c.c_int]),
+        "or_get_last_M": (c.c_int64, [c.c_void_p]),
         "or_join": (c.c_int64, [c.c_void_p]),
         "or_join_naive": (c.c_int64, [c.c_void_p]),
         "or_update_weights": (None, [c.c_void_p]),
@@ -230,6 +232,10 @@ class Job:
         if rc != 0:
             raise MemoryError("oracle round failed")
 
+    def run_attempts(self, n: int, nthreads: int = 1):
+        if lib().or_run_attempts(self._h, n, nthreads) != 0:
+            raise MemoryError
+
     def join(self) -> int:
         return int(lib().or_join(self._h))
 
@@ -337,8 +343,8 @@ class Job:
 
     @property
     def samples(self):
-        S = int(lib().or_get_last_S(self._h))
-        out = np.zeros((self.p, S * self.N), dtype=np.int32)
+        M = int(lib().or_get_last_M(self._h))
+        out = np.zeros((self.p, M), dtype=np.int32)
         lib().or_get_samples(self._h, _p(out, _i32p))
         return out
 

@@ -226,35 +226,43 @@ void or_build_table(const double *W, int L, uint32_t *T)
  * after sweep s; hist[m] += number of samples at level m; samples[k-1] =
  * level of sample k (the configuration after attempt k).
  */
+/* n consecutive attempts of one chain from its attempt t0: attempt t visits
+ * site t mod N (typewriter order continues across rounds), so a round need
+ * not start or end on a sweep.  trace gets the level at the end of every
+ * sweep completed inside the attempts. */
+int or_chain_attempts(int L, uint64_t seed, uint32_t chain, uint64_t t0, int64_t n,
+                      const uint32_t *T, int8_t *s, int32_t *m_io,
+                      int32_t *trace, int64_t *hist, int32_t *samples)
+{
+    int N = L * L;
+    int m = *m_io;
+    int64_t n_tr = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        const uint64_t t = t0 + (uint64_t)k;
+        const int site = (int)(t % (uint64_t)N);
+        int x = site % L, y = site / L;
+        int sv = SPIN(s, L, x, y);
+        int nb = SPIN(s, L, x - 1, y) + SPIN(s, L, x + 1, y) + SPIN(s, L, x, y - 1) + SPIN(s, L, x, y + 1);
+        int dE = 2 * sv * nb;
+        int a = dE / 4 + 2;
+        uint32_t u = flip_uniform(seed, chain, t);
+        if (u <= T[m * 5 + a]) {
+            s[y * L + x] = (int8_t)(-sv);
+            m += dE / 4;
+        }
+        if (hist) hist[m] += 1;
+        if (samples) samples[k] = m;
+        if (trace && site == N - 1) trace[n_tr++] = m;
+    }
+    *m_io = m;
+    return 0;
+}
+
 int or_chain_round(int L, uint64_t seed, uint32_t chain, uint64_t t0, int64_t S,
                    const uint32_t *T, int8_t *s, int32_t *m_io,
                    int32_t *trace, int64_t *hist, int32_t *samples)
 {
-    int N = L * L;
-    int m = *m_io;
-    uint64_t t = t0;
-    int64_t k = 0;
-    for (int64_t sweep = 0; sweep < S; ++sweep) {
-        for (int site = 0; site < N; ++site) {
-            int x = site % L, y = site / L;
-            int sv = SPIN(s, L, x, y);
-            int nb = SPIN(s, L, x - 1, y) + SPIN(s, L, x + 1, y) + SPIN(s, L, x, y - 1) + SPIN(s, L, x, y + 1);
-            int dE = 2 * sv * nb;
-            int a = dE / 4 + 2;
-            uint32_t u = flip_uniform(seed, chain, t);
-            t += 1;
-            if (u <= T[m * 5 + a]) {
-                s[y * L + x] = (int8_t)(-sv);
-                m += dE / 4;
-            }
-            if (hist) hist[m] += 1;
-            if (samples) samples[k] = m;
-            k += 1;
-        }
-        if (trace) trace[sweep] = m;
-    }
-    *m_io = m;
-    return 0;
+    return or_chain_attempts(L, seed, chain, t0, S * (int64_t)L * L, T, s, m_io, trace, hist, samples);
 }
 
 /*
@@ -332,7 +340,8 @@ struct or_job {
     int32_t carry;      /* level of the last configuration passed on */
     int carry_valid;
     uint32_t r;         /* rounds joined so far */
-    int64_t last_S;     /* sweeps of the last round */
+    int64_t last_S;     /* sweeps completed inside the last round (trace entries) */
+    int64_t last_M;     /* attempts (samples) per chain of the last round */
     int32_t *samples;   /* [p][M] levels of the last round's samples */
     int32_t *trace;     /* [p][S] level after each sweep */
     int64_t *k;         /* [p] first kept sample of the last joint (0 = none) */
@@ -377,7 +386,7 @@ void or_free(or_job *j)
 
 typedef struct {
     or_job *j;
-    int64_t S;
+    int64_t n, n_tr;
     int tid, nthreads;
 } round_arg;
 
@@ -385,40 +394,47 @@ static void *round_worker(void *vp)
 {
     round_arg *a = (round_arg *)vp;
     or_job *j = a->j;
-    int64_t M = a->S * (int64_t)j->N;
     for (int c = a->tid; c < j->p; c += a->nthreads)
-        or_chain_round(j->L, j->seed, (uint32_t)c, j->t, a->S, j->T,
-                       j->spins + (size_t)c * j->N, &j->m[c],
-                       j->trace + (size_t)c * (size_t)a->S, NULL,
-                       j->samples + (size_t)c * (size_t)M);
+        or_chain_attempts(j->L, j->seed, (uint32_t)c, j->t, a->n, j->T,
+                          j->spins + (size_t)c * j->N, &j->m[c],
+                          j->trace + (size_t)c * (size_t)a->n_tr, NULL,
+                          j->samples + (size_t)c * (size_t)a->n);
     return NULL;
 }
 
-/* Step 2 for every node.  Chains are independent, so they may be spread over
- * threads; the result does not depend on nthreads. */
-int or_run_round(or_job *j, int64_t S, int nthreads)
+/* Step 2 for every chain: n attempts each (a round need not be whole sweeps). */
+int or_run_attempts(or_job *j, int64_t n, int nthreads)
 {
-    if (S < 1) return -1;
-    int64_t M = S * (int64_t)j->N;
+    if (n < 1) return -1;
+    const uint64_t N = (uint64_t)j->N;
+    /* sweeps completed inside the round: attempts t with t mod N = N - 1 */
+    const int64_t n_tr = (int64_t)((j->t + (uint64_t)n) / N - j->t / N);
     free(j->samples);
     free(j->trace);
-    j->samples = (int32_t *)malloc(sizeof(int32_t) * (size_t)j->p * (size_t)M);
-    j->trace = (int32_t *)malloc(sizeof(int32_t) * (size_t)j->p * (size_t)S);
+    j->samples = (int32_t *)malloc(sizeof(int32_t) * (size_t)j->p * (size_t)n);
+    j->trace = (int32_t *)malloc(sizeof(int32_t) * (size_t)j->p * (size_t)(n_tr > 0 ? n_tr : 1));
     if (!j->samples || !j->trace) return -2;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > j->p) nthreads = j->p;
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
     round_arg *args = (round_arg *)malloc(sizeof(round_arg) * (size_t)nthreads);
     for (int q = 0; q < nthreads; ++q) {
-        args[q].j = j; args[q].S = S; args[q].tid = q; args[q].nthreads = nthreads;
+        args[q].j = j; args[q].n = n; args[q].n_tr = n_tr; args[q].tid = q; args[q].nthreads = nthreads;
         pthread_create(&th[q], NULL, round_worker, &args[q]);
     }
     for (int q = 0; q < nthreads; ++q) pthread_join(th[q], NULL);
     free(th);
     free(args);
-    j->t += (uint64_t)M;
-    j->last_S = S;
+    j->t += (uint64_t)n;
+    j->last_S = n_tr;
+    j->last_M = n;
     return 0;
+}
+
+int or_run_round(or_job *j, int64_t S, int nthreads)
+{
+    if (S < 1) return -1;
+    return or_run_attempts(j, S * (int64_t)j->N, nthreads);
 }
 
 /*
@@ -459,7 +475,7 @@ static void joint_order(or_job *j, int64_t M)
 
 int64_t or_join(or_job *j)
 {
-    int64_t M = j->last_S * (int64_t)j->N;
+    int64_t M = j->last_M;
     int64_t joined = 0;
     joint_order(j, M);
     for (int q = 0; q < j->p; ++q) {
@@ -486,7 +502,7 @@ int64_t or_join(or_job *j)
  * without the detailed-balance test at the joints. */
 int64_t or_join_naive(or_job *j)
 {
-    int64_t M = j->last_S * (int64_t)j->N;
+    int64_t M = j->last_M;
     joint_order(j, M);
     for (int q = 0; q < j->p; ++q) {
         const int i = j->order[q];
@@ -587,6 +603,7 @@ uint64_t or_get_t(const or_job *j) { return j->t; }
 void or_get_visited(const or_job *j, uint8_t *v) { memcpy(v, j->visited, (size_t)j->N + 1); }
 uint32_t or_get_round(const or_job *j) { return j->r; }
 int64_t or_get_last_S(const or_job *j) { return j->last_S; }
+int64_t or_get_last_M(const or_job *j) { return j->last_M; }
 /* Test hook: install hand-made samples for the last round (S sweeps), so that
  * the joint can be checked on crafted energy sequences. */
 int or_set_samples(or_job *j, int64_t S, const int32_t *samples)
@@ -598,12 +615,13 @@ int or_set_samples(or_job *j, int64_t S, const int32_t *samples)
     if (!j->samples) return -2;
     memcpy(j->samples, samples, sizeof(int32_t) * (size_t)j->p * (size_t)M);
     j->last_S = S;
+    j->last_M = M;
     return 0;
 }
 
 void or_get_samples(const or_job *j, int32_t *samples)
 {
-    memcpy(samples, j->samples, sizeof(int32_t) * (size_t)j->p * (size_t)(j->last_S * (int64_t)j->N));
+    memcpy(samples, j->samples, sizeof(int32_t) * (size_t)j->p * (size_t)j->last_M);
 }
 
 /* ------------------------------------------------------------------ */

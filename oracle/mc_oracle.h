@@ -64,6 +64,8 @@ typedef struct or_job or_job;
 or_job *or_create(int L, int p, uint64_t seed, int start);
 void    or_free(or_job *j);
 int     or_run_round(or_job *j, int64_t S, int nthreads);
+/* a round of n attempts per chain (attempt t visits site t mod N) */
+int     or_run_attempts(or_job *j, int64_t n, int nthreads);
 int64_t or_join(or_job *j);
 int64_t or_join_naive(or_job *j);
 /* joint order: 0 chain index (default), 1 ascending final energy (ties by index) */
@@ -90,6 +92,7 @@ uint64_t or_get_t(const or_job *j);
 void    or_get_visited(const or_job *j, uint8_t *visited);
 uint32_t or_get_round(const or_job *j);
 int64_t or_get_last_S(const or_job *j);
+int64_t or_get_last_M(const or_job *j);
 void    or_get_samples(const or_job *j, int32_t *samples);
 int     or_set_samples(or_job *j, int64_t S, const int32_t *samples);
 

@@ -187,3 +187,28 @@ def test_weight_recursion_converges_to_minus_ln_g():
         devs.append(np.abs(d - d.mean()).max())
     assert devs[0] > 1.0                                 # W=0 start is far off
     assert max(devs[-5:]) < 0.06, devs
+
+
+def test_rounds_of_any_length_compose():
+    # Sec. 2 step 2 with rounds that are not whole sweeps (Fig. 2's M_node =
+    # 100 < N): the chains' dynamics do not depend on where rounds end, so
+    # rounds of 100 attempts concatenate to the same samples, lattices and
+    # levels as whole sweeps; the trace records the level where sweeps end
+    L, p = 20, 5
+    N = L * L
+    W = np.random.default_rng(5).normal(0, 3.0, N + 1)
+    a = oracle.Job(L, p, 31, 1)
+    b = oracle.Job(L, p, 31, 1)
+    a.weights = W
+    b.weights = W
+    a.run_round(2, 2)
+    sa, ta = a.samples, a.trace
+    parts, traces = [], []
+    for _ in range(8):                         # 8 x 100 attempts = 2 sweeps
+        b.run_attempts(100, 2)
+        parts.append(b.samples)
+        traces.append(b.trace)
+    assert np.array_equal(np.concatenate(parts, axis=1), sa)
+    assert np.array_equal(np.concatenate(traces, axis=0), ta)
+    assert [t.shape[0] for t in traces] == [0, 0, 0, 1, 0, 0, 0, 1]
+    assert np.array_equal(a.spins, b.spins) and np.array_equal(a.levels, b.levels) and a.t == b.t
