@@ -96,6 +96,18 @@ int mc_set_trace(mc_job *job, int enabled);
  * n_sweeps >= 1 and n_sweeps * N < 2^34. */
 int mc_run_sweeps(mc_job *job, int64_t n_sweeps);
 
+/* Sec. 2 step 2 with M_node = n_attempts, which need not be whole sweeps
+ * (Fig. 2 uses M_node = 100 < N at L = 20): attempt t of a chain (counted
+ * from mc_init) visits site t mod N, so the typewriter order simply
+ * continues across rounds.  Whole sweeps from a sweep boundary take the
+ * mc_run_sweeps path; any other round (and any mc_run_sweeps while the
+ * chains are inside a sweep) runs one thread per chain on its lattice in
+ * global memory and is joined by the serial rule itself (meant for short
+ * rounds); no trace is recorded for such a round, and mc_batch_run refuses
+ * jobs inside a sweep.  1 <= n_attempts < 2^34.  Asynchronous; MC_ESTATE if
+ * the previous round has not been joined. */
+int mc_run_attempts(mc_job *job, int64_t n_attempts);
+
 /* Sec. 2 steps 3-5 for the last round: chain i (in order; see
  * mc_set_join_order) keeps its samples from the first one that passes the
  * Metropolis test against the energy passed on by the chains before it

@@ -20,7 +20,7 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_join_naive", "mc_histogram", "mc_update_weights", "mc_get_weights", "mc_set_weights",
     "mc_get_table", "mc_get_spins", "mc_set_spins", "mc_get_energies", "mc_get_trace",
     "mc_get_trace_chain", "mc_get_visited", "mc_set_visited", "mc_thermo", "mc_set_join_order",
-    "mc_get_order", "mc_save", "mc_load", "mc_iteration", "mc_set_join_policy",
+    "mc_get_order", "mc_save", "mc_load", "mc_iteration", "mc_set_join_policy", "mc_run_attempts",
     "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error",
     "mc_generate_noalloc", "mc_autotune", "mc_batch_run",
     "mc_job_device_bytes", "mc_server_create", "mc_server_submit", "mc_server_poll", "mc_server_wait",
@@ -100,6 +100,7 @@ def lib():
             "mc_set_stream": (ctypes.c_int, [_vp, _vp]),
             "mc_set_trace": (ctypes.c_int, [_vp, ctypes.c_int]),
             "mc_run_sweeps": (ctypes.c_int, [_vp, ctypes.c_int64]),
+            "mc_run_attempts": (ctypes.c_int, [_vp, ctypes.c_int64]),
             "mc_join": (ctypes.c_int, [_vp, _i64p]),
             "mc_join_naive": (ctypes.c_int, [_vp, _i64p]),
             "mc_histogram": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
@@ -184,6 +185,10 @@ def mc_set_trace(job, enabled: bool):
 
 def mc_run_sweeps(job, n_sweeps: int):
     _check(lib().mc_run_sweeps(job, n_sweeps))
+
+
+def mc_run_attempts(job, n_attempts: int):
+    _check(lib().mc_run_attempts(job, n_attempts))
 
 
 def mc_join(job, want_length: bool = True):
@@ -460,6 +465,9 @@ class Job:
         job.N = job.L * job.L
         job.wd = (job.L + 31) // 32
         return job
+
+    def run_attempts(self, n_attempts: int):
+        mc_run_attempts(self.h, n_attempts)
 
     def set_join_policy(self, scan_max_samples: int = -1, passes_before_scan: int = 2,
                         passes_without_scan: int = 10):

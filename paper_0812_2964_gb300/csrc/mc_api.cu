@@ -59,6 +59,8 @@ struct mc_job {
   uint64_t t = 0;       // attempts per chain so far
   uint32_t r = 0;       // joints done
   int64_t last_S = 0;
+  int64_t last_M = 0;           // attempts per chain of the last round
+  bool attempts_round = false;  // the last round was not whole sweeps from a sweep start
   bool pending = false;
   bool trace_on = false;
   bool trace_valid = false;
@@ -359,8 +361,31 @@ int round_prepare(mc_job* job, int64_t n_sweeps, uint64_t* t0) {
   *t0 = job->t;
   job->t += static_cast<uint64_t>(M);
   job->last_S = n_sweeps;
+  job->last_M = M;
+  job->attempts_round = false;
   job->pending = true;
   job->trace_valid = job->trace_on;
+  return MC_OK;
+}
+
+// A round of n attempts that does not start or end on a sweep: round-start
+// copies for the serial joint's replays; no checkpoints, no trace.
+int attempts_prepare(mc_job* job, int64_t n, uint64_t* t0) {
+  if (job->pending) return fail(MC_ESTATE, "previous round not joined");
+  if (n < 1 || n >= (int64_t(1) << 34)) return fail(MC_EINVAL, "n_attempts=%lld", static_cast<long long>(n));
+  DevJob& d = job->d;
+  const size_t lat = static_cast<size_t>(job->p) * job->L * job->wd;
+  MC_CUDA(cudaMemcpyAsync(d.spins0, d.spins, lat * sizeof(uint32_t), cudaMemcpyDeviceToDevice, job->stream),
+          "round-start copy");
+  MC_CUDA(cudaMemcpyAsync(d.m0, d.m, job->p * sizeof(int32_t), cudaMemcpyDeviceToDevice, job->stream),
+          "round-start copy");
+  *t0 = job->t;
+  job->t += static_cast<uint64_t>(n);
+  job->last_S = n / job->N;
+  job->last_M = n;
+  job->attempts_round = true;
+  job->pending = true;
+  job->trace_valid = false;
   return MC_OK;
 }
 
@@ -368,8 +393,24 @@ int round_prepare(mc_job* job, int64_t n_sweeps, uint64_t* t0) {
 
 extern "C" {
 
+int mc_run_attempts(mc_job* job, int64_t n_attempts) {
+  if (int rc = check_job(job)) return rc;
+  const int64_t N = job->N;
+  if (n_attempts >= 1 && n_attempts % N == 0 && job->t % static_cast<uint64_t>(N) == 0)
+    return mc_run_sweeps(job, n_attempts / N);
+  uint64_t t0 = 0;
+  if (int rc = attempts_prepare(job, n_attempts, &t0)) return rc;
+  MC_CUDA(mcgpu::k_generate_attempts(job->d, t0, n_attempts, job->stream), "generation");
+  return MC_OK;
+}
+
 int mc_run_sweeps(mc_job* job, int64_t n_sweeps) {
   if (int rc = check_job(job)) return rc;
+  if (job->t % static_cast<uint64_t>(job->N) != 0) {   // chains are inside a sweep
+    if (n_sweeps < 1 || n_sweeps > (int64_t(1) << 34) / job->N)
+      return fail(MC_EINVAL, "n_sweeps=%lld", static_cast<long long>(n_sweeps));
+    return mc_run_attempts(job, n_sweeps * job->N);
+  }
   uint64_t t0 = 0;
   if (int rc = round_prepare(job, n_sweeps, &t0)) return rc;
   MC_CUDA(mcgpu::k_generate(job->d, job->shape, t0, n_sweeps, job->trace_on, job->stream), "generation");
@@ -379,10 +420,14 @@ int mc_run_sweeps(mc_job* job, int64_t n_sweeps) {
 static int join_common(mc_job* job, int64_t* joined_len, bool naive) {
   if (int rc = check_job(job)) return rc;
   if (!job->pending) return fail(MC_ESTATE, "no round to join");
-  const int64_t M = job->last_S * job->N;
-  MC_CUDA(mcgpu::k_join(job->d, job->shape, job->t - static_cast<uint64_t>(M), job->last_S, job->r, naive,
-                        job->stream),
-          "joint");
+  const int64_t M = job->last_M;
+  if (job->attempts_round)
+    MC_CUDA(mcgpu::k_join_attempts(job->d, job->t - static_cast<uint64_t>(M), M, job->r, naive, job->stream),
+            "joint");
+  else
+    MC_CUDA(mcgpu::k_join(job->d, job->shape, job->t - static_cast<uint64_t>(M), job->last_S, job->r, naive,
+                          job->stream),
+            "joint");
   job->r += 1;
   job->pending = false;
   if (joined_len) {
@@ -460,6 +505,8 @@ int mc_batch_run(mc_job** jobs, int n_jobs, int iterations, int64_t n_sweeps, in
   for (int i = 0; i < n_jobs; ++i) {
     if (!jobs[i]) return fail(MC_EINVAL, "job %d is null", i);
     if (jobs[i]->pending) return fail(MC_ESTATE, "job %d has a round pending", i);
+    if (jobs[i]->t % static_cast<uint64_t>(jobs[i]->N) != 0)
+      return fail(MC_EINVAL, "job %d is inside a sweep: batches run whole sweeps", i);
     if (jobs[i]->device != jobs[0]->device) return fail(MC_EINVAL, "jobs on different devices");
     for (int k = 0; k < i; ++k)
       if (jobs[k] == jobs[i]) return fail(MC_EINVAL, "job %d listed twice", i);

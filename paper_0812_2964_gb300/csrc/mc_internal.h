@@ -86,6 +86,10 @@ cudaError_t k_order(const DevJob& j, cudaStream_t st);
 cudaError_t k_levels(const DevJob& j, cudaStream_t st);
 cudaError_t k_build_table(const DevJob& j, cudaStream_t st);
 cudaError_t k_update_weights(const DevJob& j, cudaStream_t st);
+// rounds that are not whole sweeps: n attempts per chain from attempt t0,
+// and their joint by the serial rule (M attempts per chain)
+cudaError_t k_generate_attempts(const DevJob& j, uint64_t t0, int64_t n, cudaStream_t st);
+cudaError_t k_join_attempts(const DevJob& j, uint64_t t0, int64_t M, uint32_t r, bool naive, cudaStream_t st);
 // E, C, F, S at n inverse temperatures (device arrays betas[n], out[n][4])
 cudaError_t k_thermo(const DevJob& j, const double* betas, int n, double* out, cudaStream_t st);
 cudaError_t k_generate(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S,

@@ -257,10 +257,9 @@ __global__ void __launch_bounds__(1024) order_kernel(const DevJob j) {
 
 // Segmented scan and histogram: kept length of chain i is M - k_i + 1 (0 if
 // nothing is kept); offsets are the exclusive scan; h += hgen - dpre.
-__global__ void __launch_bounds__(1024) finalize_kernel(const DevJob j, const int64_t S) {
+__global__ void __launch_bounds__(1024) finalize_kernel(const DevJob j, const int64_t M) {
   __shared__ long long s_tmp[1024];
   const int t = threadIdx.x, nt = blockDim.x;
-  const int64_t M = S * j.N;
   for (int m = t; m < j.np1; m += nt) {
     j.h[m] += static_cast<long long>(j.hgen[m] - j.dpre[m]);
     j.hgen[m] = 0ull;
@@ -536,6 +535,121 @@ __global__ void __launch_bounds__(1024) nohit_kernel(const DevJob j, const int l
   if (threadIdx.x == 0) j.stats[kStatNoHit] = s_count;
 }
 
+// ------------------------------------------------------------------ rounds of any length
+// Rounds that do not start or end on a sweep (Fig. 2's M_node = 100 < N):
+// attempt t of a chain visits site t mod N and draws word t&3 of Philox
+// block t>>2, with the thresholds and the acceptance rule of the sweep
+// kernels, so the chains are the same whichever kernel runs them.  Meant for
+// short rounds: one thread per chain works straight on its bit-packed
+// lattice in global memory and counts every sample into hgen.
+__device__ __forceinline__ int site_spin(const uint32_t* lat, int wd, int L, int x, int y) {
+  x = (x + L) % L;
+  y = (y + L) % L;
+  return static_cast<int>((lat[y * wd + (x >> 5)] >> (x & 31)) & 1u);
+}
+
+// one attempt: returns the new level; flips the site in lat if accepted
+__device__ __forceinline__ int attempt_one(const DevJob& j, uint32_t* lat, int m, uint64_t t, uint32_t chain,
+                                           uint4& r, uint64_t& blk) {
+  const int site = static_cast<int>(t % static_cast<uint64_t>(j.N));
+  const int x = site % j.L, y = site / j.L;
+  const int sv = site_spin(lat, j.wd, j.L, x, y);
+  const int a = (site_spin(lat, j.wd, j.L, x - 1, y) == sv) + (site_spin(lat, j.wd, j.L, x + 1, y) == sv) +
+                (site_spin(lat, j.wd, j.L, x, y - 1) == sv) + (site_spin(lat, j.wd, j.L, x, y + 1) == sv);
+  if ((t >> 2) != blk) {
+    blk = t >> 2;
+    r = philox4x32_10(make_uint4(static_cast<uint32_t>(blk), static_cast<uint32_t>(blk >> 32), chain, kTagFlip),
+                      j.key0, j.key1);
+  }
+  const uint32_t u = uint4_word(r, static_cast<uint32_t>(t & 3u));
+  if (u <= j.T[a * j.np1 + m]) {
+    lat[y * j.wd + (x >> 5)] ^= 1u << (x & 31);
+    m += a - 2;
+  }
+  return m;
+}
+
+__global__ void attempts_kernel(const DevJob j, const uint64_t t0, const int64_t n) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= j.p) return;
+  uint32_t* lat = j.spins + static_cast<size_t>(c) * j.L * j.wd;
+  int m = j.m[c];
+  uint4 r = make_uint4(0u, 0u, 0u, 0u);
+  uint64_t blk = ~0ull;
+  for (int64_t k = 0; k < n; ++k) {
+    m = attempt_one(j, lat, m, t0 + static_cast<uint64_t>(k), static_cast<uint32_t>(c), r, blk);
+    atomicAdd(&j.hgen[m], 1ull);
+  }
+  j.m[c] = m;
+}
+
+// The joint of such a round by the serial rule itself (Sec. 2 steps 3-5),
+// one thread: each chain, in joint order, is regenerated from its round
+// start until its first sample that passes the test against the level
+// passed on; the samples before it go to dpre.
+constexpr int kMaxLatWords = 128 * 4;
+__global__ void serial_joint_kernel(const DevJob j, const uint64_t t0, const int64_t M, const uint32_t r) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int carry_valid = static_cast<int>(j.stats[kStatCarryValid]);
+  int carry = static_cast<int>(j.stats[kStatCarry]);
+  uint32_t lat[kMaxLatWords];
+  long long searched = 0;
+  for (int q = 0; q < j.p; ++q) {
+    const int c = j.perm[q];
+    int64_t kf = 0;
+    j.xused[c] = carry_valid ? carry : -1;
+    if (!carry_valid) {
+      kf = 1;
+    } else {
+      const uint32_t* src = j.spins0 + static_cast<size_t>(c) * j.L * j.wd;
+      for (int w = 0; w < j.L * j.wd; ++w) lat[w] = src[w];
+      int m = j.m0[c];
+      uint4 fr = make_uint4(0u, 0u, 0u, 0u), jr = fr;
+      uint64_t blk = ~0ull;
+      const double wx = j.W[carry];
+      for (int64_t k = 1; k <= M; ++k) {
+        m = attempt_one(j, lat, m, t0 + static_cast<uint64_t>(k - 1), static_cast<uint32_t>(c), fr, blk);
+        const uint64_t qk = static_cast<uint64_t>(k - 1);
+        if ((qk & 3u) == 0u || k == 1)
+          jr = philox4x32_10(make_uint4(static_cast<uint32_t>(qk >> 2), r, static_cast<uint32_t>(c), kTagJoint),
+                             j.key0, j.key1);
+        ++searched;
+        if (uint4_word(jr, static_cast<uint32_t>(qk & 3u)) <= threshold_det(__dsub_rn(j.W[m], wx))) {
+          kf = k;
+          break;
+        }
+        j.dpre[m] += 1ull;   // a discarded sample
+      }
+    }
+    j.k[c] = kf;
+    if (kf > 0) {
+      carry = j.m[c];
+      carry_valid = 1;
+    }
+  }
+  j.stats[kStatCarry] = carry;
+  j.stats[kStatCarryValid] = carry_valid;
+  j.stats[kStatMismatch] = 0;
+  j.stats[kStatPasses] = 0;
+  j.stats[kStatScanned] = 0;
+  j.stats[kStatSearched] = searched;
+}
+
+cudaError_t k_generate_attempts(const DevJob& j, uint64_t t0, int64_t n, cudaStream_t st) {
+  attempts_kernel<<<blocks_for(j.p, 128), 128, 0, st>>>(j, t0, n);
+  launches_add(1);
+  return cudaGetLastError();
+}
+
+cudaError_t k_join_attempts(const DevJob& j, uint64_t t0, int64_t M, uint32_t r, bool naive, cudaStream_t st) {
+  order_kernel<<<1, 1024, 0, st>>>(j);
+  if (naive) naive_kernel<<<blocks_for(j.p, 256), 256, 0, st>>>(j);
+  else serial_joint_kernel<<<1, 32, 0, st>>>(j, t0, M, r);
+  finalize_kernel<<<1, 1024, 0, st>>>(j, M);
+  launches_add(3);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ host side
 size_t gen_smem_bytes(int L, const LaunchShape& s, bool* table_in_smem) {
   const bool ts = table_fits(L, s, true);
@@ -732,7 +846,7 @@ cudaError_t join_tj_list(const DevJob& j, cudaStream_t st) {
 }
 
 cudaError_t join_finalize(const DevJob& j, int64_t S, cudaStream_t st) {
-  finalize_kernel<<<1, 1024, 0, st>>>(j, S);
+  finalize_kernel<<<1, 1024, 0, st>>>(j, S * j.N);
   launches_add(1);
   return cudaGetLastError();
 }
@@ -770,7 +884,7 @@ cudaError_t k_join(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S
   if (naive) {
     order_kernel<<<1, 1024, 0, st>>>(j);
     naive_kernel<<<blocks_for(j.p, 256), 256, 0, st>>>(j);
-    finalize_kernel<<<1, 1024, 0, st>>>(j, S);
+    finalize_kernel<<<1, 1024, 0, st>>>(j, S * j.N);
     launches_add(3);
     return cudaGetLastError();
   }
