@@ -481,8 +481,7 @@ def run_fig2(args):
     (mc_join) and simply concatenated (mc_join_naive) -- each iteration
     collecting M_total samples in rounds of M_node attempts per chain; then
     E/N by Eq. (reweighting2) against the exact finite-lattice values.
-    M_node is one sweep (N = 400 attempts; the paper's 100 is a partial
-    sweep, which this library's rounds do not make)."""
+    M_node = 100 attempts (a quarter sweep: mc_run_attempts)."""
     import torch
 
     import paper_0812_2964_gb300 as mc
@@ -493,7 +492,7 @@ def run_fig2(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     mc.build()
-    L, p, S = 20, 32, 1
+    L, p, M_node = 20, 32, args.mnode
     N = L * L
     M_total = args.mtotal
     iters = args.iters
@@ -507,7 +506,7 @@ def run_fig2(args):
         for _ in range(iters):
             got = 0
             while got < M_total:
-                job.run_sweeps(S)
+                job.run_attempts(M_node)
                 got += job.join_naive() if naive else job.join()
                 rounds += 1
             job.update_weights()
@@ -522,7 +521,7 @@ def run_fig2(args):
     line = {"metric": "fig2: E/N deviation from the exact L=20 values", "unit": "energy per site",
             "value": out["detailed balance"]["max_abs_dev_beta_le_0.44"], "higher_is_better": False,
             "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": "fig2", "L": L, "chains": p, "M_node_attempts": S * N, "M_total": M_total,
+            "config": {"workload": "fig2", "L": L, "chains": p, "M_node_attempts": M_node, "M_total": M_total,
                        "iterations": iters, "betas": betas},
             "exact_E_per_site": exact, "runs": out}
     if rank == 0:
@@ -548,8 +547,9 @@ def main(argv=None):
     ap.add_argument("--slots", type=int, default=64, help="serving: server slots")
     ap.add_argument("--join-order", type=int, default=0,
                     help="0: chains joined in index order; 1: by ascending final energy (end of Sec. 2)")
-    ap.add_argument("--mtotal", type=int, default=10_000_000, help="fig2: samples per weight iteration")
-    ap.add_argument("--iters", type=int, default=40, help="fig2: weight iterations")
+    ap.add_argument("--mtotal", type=int, default=1_000_000, help="fig2: samples per weight iteration")
+    ap.add_argument("--iters", type=int, default=20, help="fig2: weight iterations")
+    ap.add_argument("--mnode", type=int, default=100, help="fig2: attempts per chain per round (M_node)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
