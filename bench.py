@@ -37,10 +37,11 @@ from paper_0812_2964_gb300.workloads import WORKLOADS  # noqa: E402
 METRIC = "joined-chain spin-flip attempts/s"
 UNIT = "attempts/s"
 WORKLOAD = "L32_p16384"
-# Integer operations one single-spin-flip attempt needs (derivation in
-# the design doc): Philox4x32-10 amortised over its 4 words (10), aligned-
-# neighbour count (7), threshold index + load (2), compare (1), flip + level
-# update (2), histogram update (3).
+# Integer operations one single-spin-flip attempt needs: Philox4x32-10
+# amortised over its 4 words (10 rounds x (2 multiplies + 2 three-input
+# XORs) / 4 = 10), aligned-neighbour count (4 compares + 3 adds = 7),
+# threshold index + load (2), compare (1), flip + level update (2),
+# histogram update (3).
 ALG_OPS_PER_ATTEMPT = 25
 SMS, SUBPARTITIONS, LANES = 152, 4, 32
 L2_FLUSH_BYTES = 256 << 20
