@@ -262,7 +262,18 @@ int mc_server_create(uint64_t budget_bytes, int max_slots, mc_server** out) {
     delete srv;
     return e == cudaErrorMemoryAllocation ? MC_ENOMEM : MC_ECUDA;
   }
-  srv->worker = std::thread(worker_main, srv);
+  try {
+    srv->worker = std::thread(worker_main, srv);
+  } catch (...) {  // no thread: release everything, nothing crosses the ABI
+    for (auto& sl : srv->slots) {
+      for (auto& ev : sl.ev)
+        if (ev) cudaEventDestroy(ev);
+      if (sl.st) cudaStreamDestroy(sl.st);
+    }
+    delete srv;
+    mcgpu::set_last_error("mc_server_create: could not start the server thread");
+    return MC_ENOMEM;
+  }
   *out = srv;
   return MC_OK;
 }
@@ -280,14 +291,20 @@ int mc_server_submit(mc_server* srv, const mc_jobspec* spec, uint64_t* id) {
     mcgpu::set_last_error("mc_server_submit: the job alone exceeds the device-memory budget");
     return MC_ENOMEM;
   }
-  auto r = std::make_unique<Rec>();
+  std::unique_ptr<Rec> r(new (std::nothrow) Rec());
+  if (!r) return MC_ENOMEM;
   r->id = srv->next_id++;
   r->spec = *spec;
   r->bytes = bytes;
   r->t_submit = srv->now();
   *id = r->id;
-  srv->queue.push_back(r.get());
-  srv->recs.emplace(r->id, std::move(r));
+  try {
+    srv->queue.push_back(r.get());
+    srv->recs.emplace(r->id, std::move(r));
+  } catch (...) {
+    if (!srv->queue.empty() && r && srv->queue.back() == r.get()) srv->queue.pop_back();
+    return MC_ENOMEM;
+  }
   srv->cv_work.notify_one();
   return MC_OK;
 }
