@@ -148,7 +148,7 @@ const char* mc_last_error(void) { return g_err.c_str(); }
 
 uint64_t mc_kernel_launches(void) { return mcgpu::launches_add(0); }
 
-int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
+static int mc_init_impl(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
   if (!out) return fail(MC_EINVAL, "out is null");
   *out = nullptr;
   if (L < 4 || L > 128 || (L % 4) != 0) return fail(MC_EINVAL, "L=%d: need 4 <= L <= 128, L %% 4 == 0", L);
@@ -225,6 +225,17 @@ int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
   j->shape = mcgpu::default_shape(L, n_chains, j->num_sms);
   *out = j;
   return MC_OK;
+}
+
+// (host allocations inside may throw; nothing crosses the ABI)
+int mc_init(int L, int n_chains, uint64_t seed, int start, mc_job** out) {
+  try {
+    return mc_init_impl(L, n_chains, seed, start, out);
+  } catch (const std::bad_alloc&) {
+    return fail(MC_ENOMEM, "mc_init: host allocation failed");
+  } catch (...) {
+    return fail(MC_EINVAL, "mc_init: unexpected host error");
+  }
 }
 
 void mc_free(mc_job* job) {
@@ -497,7 +508,7 @@ int mc_update_weights(mc_job* job) {
 // per job; 1: one fused generation launch for all jobs that fit it (others
 // keep their own launch); 2: as 1, with the whole loop captured once as a
 // CUDA graph and launched.  Results are identical in all modes.
-int mc_batch_run(mc_job** jobs, int n_jobs, int iterations, int64_t n_sweeps, int mode) {
+static int mc_batch_run_impl(mc_job** jobs, int n_jobs, int iterations, int64_t n_sweeps, int mode) {
   if (!jobs || n_jobs < 1) return fail(MC_EINVAL, "no jobs");
   if (mode < 0 || mode > 2) return fail(MC_EINVAL, "mode=%d: 0 per-job, 1 fused, 2 fused + graph", mode);
   if (iterations < 1) return fail(MC_EINVAL, "iterations=%d", iterations);
@@ -615,6 +626,17 @@ int mc_batch_run(mc_job** jobs, int n_jobs, int iterations, int64_t n_sweeps, in
   return MC_OK;
 }
 
+// (host allocations inside may throw; nothing crosses the ABI)
+int mc_batch_run(mc_job** jobs, int n_jobs, int iterations, int64_t n_sweeps, int mode) {
+  try {
+    return mc_batch_run_impl(jobs, n_jobs, iterations, n_sweeps, mode);
+  } catch (const std::bad_alloc&) {
+    return fail(MC_ENOMEM, "mc_batch_run: host allocation failed");
+  } catch (...) {
+    return fail(MC_EINVAL, "mc_batch_run: unexpected host error");
+  }
+}
+
 int mc_get_weights(mc_job* job, double* out, int n) {
   if (int rc = check_job(job)) return rc;
   if (!out || n != job->N + 1) return fail(MC_EINVAL, "weights need N+1 = %d entries", job->N + 1);
@@ -638,7 +660,7 @@ int mc_get_visited(mc_job* job, uint8_t* out, int n) {
   return sync(job, "visited");
 }
 
-int mc_set_visited(mc_job* job, const uint8_t* in, int n) {
+static int mc_set_visited_impl(mc_job* job, const uint8_t* in, int n) {
   if (int rc = check_job(job)) return rc;
   if (job->pending) return fail(MC_ESTATE, "round pending");
   if (!in || n != job->N + 1) return fail(MC_EINVAL, "visited mask needs N+1 = %d entries", job->N + 1);
@@ -646,6 +668,17 @@ int mc_set_visited(mc_job* job, const uint8_t* in, int n) {
   for (auto& x : v) x = x ? 1 : 0;
   MC_CUDA(cudaMemcpyAsync(job->d.visited, v.data(), n, cudaMemcpyHostToDevice, job->stream), "visited copy");
   return sync(job, "visited");
+}
+
+// (host allocations inside may throw; nothing crosses the ABI)
+int mc_set_visited(mc_job* job, const uint8_t* in, int n) {
+  try {
+    return mc_set_visited_impl(job, in, n);
+  } catch (const std::bad_alloc&) {
+    return fail(MC_ENOMEM, "mc_set_visited: host allocation failed");
+  } catch (...) {
+    return fail(MC_EINVAL, "mc_set_visited: unexpected host error");
+  }
 }
 
 // ------------------------------------------------------------------ save / load
@@ -666,7 +699,7 @@ struct FileHeader {
 };
 }  // namespace
 
-int mc_save(mc_job* job, const char* path) {
+static int mc_save_impl(mc_job* job, const char* path) {
   if (int rc = check_job(job)) return rc;
   if (!path) return fail(MC_EINVAL, "path is null");
   if (job->pending) return fail(MC_ESTATE, "round pending: join first");
@@ -703,7 +736,18 @@ int mc_save(mc_job* job, const char* path) {
   return ok ? MC_OK : fail(MC_EINVAL, "write to %s failed", path);
 }
 
-int mc_load(const char* path, mc_job** out) {
+// (host allocations inside may throw; nothing crosses the ABI)
+int mc_save(mc_job* job, const char* path) {
+  try {
+    return mc_save_impl(job, path);
+  } catch (const std::bad_alloc&) {
+    return fail(MC_ENOMEM, "mc_save: host allocation failed");
+  } catch (...) {
+    return fail(MC_EINVAL, "mc_save: unexpected host error");
+  }
+}
+
+static int mc_load_impl(const char* path, mc_job** out) {
   if (!out) return fail(MC_EINVAL, "out is null");
   *out = nullptr;
   if (!path) return fail(MC_EINVAL, "path is null");
@@ -750,6 +794,17 @@ int mc_load(const char* path, mc_job** out) {
   j->d.ordered = hd.order;
   *out = j;
   return MC_OK;
+}
+
+// (host allocations inside may throw; nothing crosses the ABI)
+int mc_load(const char* path, mc_job** out) {
+  try {
+    return mc_load_impl(path, out);
+  } catch (const std::bad_alloc&) {
+    return fail(MC_ENOMEM, "mc_load: host allocation failed");
+  } catch (...) {
+    return fail(MC_EINVAL, "mc_load: unexpected host error");
+  }
 }
 
 int mc_set_join_policy(mc_job* job, int64_t scan_max_samples, int passes_before_scan, int passes_without_scan) {
@@ -811,7 +866,7 @@ int mc_get_spins(mc_job* job, uint32_t* out, size_t n_words) {
   return sync(job, "spins");
 }
 
-int mc_set_spins(mc_job* job, const uint32_t* in, size_t n_words) {
+static int mc_set_spins_impl(mc_job* job, const uint32_t* in, size_t n_words) {
   if (int rc = check_job(job)) return rc;
   if (job->pending) return fail(MC_ESTATE, "round pending");
   const size_t need = static_cast<size_t>(job->p) * job->L * job->wd;
@@ -823,6 +878,17 @@ int mc_set_spins(mc_job* job, const uint32_t* in, size_t n_words) {
   MC_CUDA(cudaMemcpyAsync(job->d.spins, tmp.data(), need * 4, cudaMemcpyHostToDevice, job->stream), "spins copy");
   MC_CUDA(mcgpu::k_levels(job->d, job->stream), "levels");
   return sync(job, "set spins");
+}
+
+// (host allocations inside may throw; nothing crosses the ABI)
+int mc_set_spins(mc_job* job, const uint32_t* in, size_t n_words) {
+  try {
+    return mc_set_spins_impl(job, in, n_words);
+  } catch (const std::bad_alloc&) {
+    return fail(MC_ENOMEM, "mc_set_spins: host allocation failed");
+  } catch (...) {
+    return fail(MC_EINVAL, "mc_set_spins: unexpected host error");
+  }
 }
 
 int mc_get_energies(mc_job* job, int32_t* out, int n) {
@@ -905,7 +971,7 @@ std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, LaunchShape> g_tune_cache;
 }  // namespace
 
-int mc_autotune(mc_job* job, int64_t probe_sweeps, int use_cache, int* placement, int* cpw, int* wpb) {
+static int mc_autotune_impl(mc_job* job, int64_t probe_sweeps, int use_cache, int* placement, int* cpw, int* wpb) {
   if (int rc = check_job(job)) return rc;
   if (job->pending) return fail(MC_ESTATE, "round pending");
   if (probe_sweeps < 1 || probe_sweeps * job->N >= (int64_t(1) << 34)) return fail(MC_EINVAL, "bad probe_sweeps");
@@ -991,6 +1057,17 @@ int mc_autotune(mc_job* job, int64_t probe_sweeps, int use_cache, int* placement
   if (cpw) *cpw = best.cpw;
   if (wpb) *wpb = best.wpb;
   return MC_OK;
+}
+
+// (host allocations inside may throw; nothing crosses the ABI)
+int mc_autotune(mc_job* job, int64_t probe_sweeps, int use_cache, int* placement, int* cpw, int* wpb) {
+  try {
+    return mc_autotune_impl(job, probe_sweeps, use_cache, placement, cpw, wpb);
+  } catch (const std::bad_alloc&) {
+    return fail(MC_ENOMEM, "mc_autotune: host allocation failed");
+  } catch (...) {
+    return fail(MC_EINVAL, "mc_autotune: unexpected host error");
+  }
 }
 
 uint64_t mc_job_device_bytes(int L, int n_chains, int64_t sweeps) {
