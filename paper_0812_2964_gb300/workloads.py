@@ -87,8 +87,11 @@ def serving_stream(n_jobs: int, rate: float = 20.0, sweeps: int = 20, seed: int 
     weight iterations uniform over 20..60, `sweeps` sweeps per iteration,
     job seed 1000 + index."""
     rng = np.random.default_rng(seed)
-    t = np.cumsum(rng.exponential(1.0 / rate, n_jobs))
-    Ls = rng.choice(np.array(SERVING_SIZES), n_jobs)
-    ps = 256 * rng.integers(1, 17, n_jobs)
-    its = rng.integers(20, 61, n_jobs)
-    return [ServedJob(float(t[i]), int(Ls[i]), int(ps[i]), int(its[i]), sweeps, 1000 + i) for i in range(n_jobs)]
+    out, t = [], 0.0
+    for i in range(n_jobs):        # job by job, so a shorter stream is a prefix of a longer one
+        t += float(rng.exponential(1.0 / rate))
+        L = int(rng.choice(np.array(SERVING_SIZES)))
+        p = 256 * int(rng.integers(1, 17))
+        its = int(rng.integers(20, 61))
+        out.append(ServedJob(t, L, p, its, sweeps, 1000 + i))
+    return out
