@@ -1,6 +1,8 @@
 """The GPU row sweep (bit-parallel neighbour counts, Philox prefetch,
-dwell-time histogram) compiled for the host and checked against the oracle
-for every supported lattice size, before any of it runs on a GPU."""
+dwell-time histogram) and the joint's replay hooks (per-word joint
+uniforms, first accepted sample, per-level minimum uniforms) compiled for
+the host and checked against the oracle for every supported lattice size,
+before any of it runs on a GPU."""
 import os
 import shutil
 import subprocess
