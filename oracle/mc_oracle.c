@@ -5,8 +5,13 @@
  * test suite, the smoke check and the benchmark's CPU-baseline leg load it;
  * the GPU library shares no code with it.  Everything is written to be read
  * against the paper:
- *   Sec. 2, "Algorithm", steps 1-6 ......... or_run_round / or_join / or_iteration
+ *   Sec. 2, "Algorithm", steps 1-6 ......... or_run_round / or_run_attempts /
+ *                                             or_join / or_iteration
+ *   Sec. 2, step 6 with M_node adjusted ..... or_iteration_adaptive
+ *   Sec. 2, energy-ordered joining .......... or_set_join_order (opt-in)
+ *   Sec. 5, Fig. 2 control (no balance) ..... or_join_naive
  *   Sec. 3.1, Eq. (new_weight) .............. or_update_weights
+ *   Sec. 3.2, Eq. (reweighting2), Sec. 4.1 .. or_thermo (E, C, F, S)
  *   Sec. 4.1, the Hamiltonian ............... or_energy
  *   Sec. 4.2, weights kept as logarithms .... W = ln w, W -= ln h
  *   Sec. 4.2, "The Metropolis method" ....... or_threshold (flips and joints)
