@@ -218,6 +218,8 @@ def run_gpu(args):
         job.set_join_order(args.join_order)
     if args.tune:
         job.autotune(probe_sweeps=max(1, min(S, 4_000_000 // N)))
+    if args.segment_samples:
+        job.set_segment_samples(args.segment_samples)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
 
     with torch.cuda.stream(stream):
@@ -238,24 +240,31 @@ def run_gpu(args):
     launches0 = mc.mc_kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    gen = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+    # per step: events before generation, the joint, the weight update and the L2 flush
+    marks = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     with torch.cuda.stream(stream):
         ev0.record(stream)
         for i in range(args.steps):
-            gen[i][0].record(stream)
-            job.run_sweeps(S)              # generation kernel (+ 2 MB round-start copy)
-            gen[i][1].record(stream)
+            e = marks[i]
+            e[0].record(stream)
+            job.run_sweeps(S)              # generation kernel (+ round-start copy)
+            e[1].record(stream)
             job.join(want_length=False)    # joint: search, resolution, correction, scan
+            e[2].record(stream)
             job.update_weights()           # Eq. (new_weight) + threshold table
+            e[3].record(stream)
             flush.fill_(1)                 # L2 flushed between timed steps
+            e[4].record(stream)
         ev1.record(stream)
     torch.cuda.synchronize()
     launches = mc.mc_kernel_launches() - launches0
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     kept = job.info()["total_joined"] - kept0
-    gen_ms = [a.elapsed_time(b) for a, b in gen]
+    gen_ms = [e[0].elapsed_time(e[1]) for e in marks]
+    phases = {name: statistics.mean(e[a].elapsed_time(e[a + 1]) for e in marks)
+              for a, name in enumerate(("gen_ms", "joint_ms", "update_ms", "l2_flush_ms"))}
+    phases["joint_ms_max"] = max(e[1].elapsed_time(e[2]) for e in marks)
     info = job.info()
     if world > 1:
         dist.barrier()
@@ -302,11 +311,16 @@ def run_gpu(args):
     gen_attempts = p * M
     achieved = gen_attempts * ALG_OPS_PER_ATTEMPT / gen_s
     tr = _traffic_record()
-    traffic = tr.get("bytes_per_launch") if (tr.get("workload") == args.workload and tr.get("sweeps") == S
-                                             and tr.get("kernel_rev") == mc.KERNEL_REV) else None
-    # issue-slot use of the same kernel measured by ncu (the 50 % target is on this)
-    issue = tr.get("issue_active_pct") if (tr.get("workload") == args.workload
-                                            and tr.get("kernel_rev") == mc.KERNEL_REV) else None
+    same_kernel = tr.get("workload") == args.workload and tr.get("kernel_rev") == mc.KERNEL_REV
+    traffic = None
+    if same_kernel and tr.get("bytes_per_launch") and tr.get("sweeps"):
+        # captured on a shorter launch of the same kernel and scaled to this
+        # one: the trace grows with the sweeps, the rest is per launch
+        per_sweep = tr.get("bytes_per_sweep", 0)
+        traffic = tr["bytes_per_launch"] + per_sweep * (S - tr["sweeps"])
+    # issue-slot use of the same kernel revision measured by ncu on the capture
+    # case named in the source (a shorter launch of the same workload)
+    issue = tr.get("issue_active_pct") if same_kernel else None
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -325,6 +339,7 @@ def run_gpu(args):
                               "warps_per_block": info["warps_per_block"]},
                    "parallelism": f"replicas x{world}",
                    "join_order": ["chain index", "ascending final energy"][args.join_order]},
+        "phases": phases,
         "kept_fraction": kept / (args.steps * p * M),
         "raw_attempts_per_s": args.steps * p * M * world / t_max,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
@@ -333,7 +348,10 @@ def run_gpu(args):
                      "kernel_ms": statistics.mean(gen_ms),
                      "ops_per_attempt": ALG_OPS_PER_ATTEMPT,
                      "measured_issue_active": (issue / 100.0) if issue is not None else None,
+                     "measured_issue_lane_weighted": (issue / 100.0 * tr.get("lanes_active", 32) / 32)
+                     if issue is not None else None,
                      "measured_issue_source": tr.get("issue_active_source") if issue is not None else None,
+                     "traffic_source": tr.get("traffic_source") if traffic is not None else None,
                      "peak_source": f"{SMS} SMs x {SUBPARTITIONS} sub-partitions x {LANES} lanes x "
                                     f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"},
         "e2e": {"value": e2e_all / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -341,7 +359,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
         "last_joint": {k: info[k] for k in ("last_joined", "last_rejected", "last_mismatch",
-                                            "last_passes", "last_searched")},
+                                            "last_passes", "last_searched", "segments", "segment_sweeps")},
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
@@ -540,6 +558,8 @@ def main(argv=None):
                     help="L32_p16384 (default), L64_p4096, L128_p1024, L8_p64, batch_uneven, serving or fig2")
     ap.add_argument("--sweeps", type=int, default=0, help="override sweeps per iteration")
     ap.add_argument("--tune", action="store_true", help="pick the launch shape with mc_autotune first")
+    ap.add_argument("--segment-samples", type=int, default=0,
+                    help="target length of the joint's checkpoint segments (0: the library's default)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

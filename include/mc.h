@@ -68,6 +68,8 @@ typedef struct mc_info {
   int chains_per_warp, warps_per_block;
   size_t device_bytes;         /* device memory held by the job */
   int64_t last_scanned;        /* chains the exact scan settled (0: speculation sufficed) */
+  int segments;                /* checkpoint segments of the most recent whole-sweep round */
+  int segment_sweeps;          /* sweeps per segment of that round */
 } mc_info;
 
 /* Create a job: Sec. 2 step 1 (h = 0, initial configurations C_1) and
@@ -160,6 +162,20 @@ int mc_set_weights(mc_job *job, const double *w, int n);
  * to the one-block fallback.  Passes in 0..64 (defaults 2 and 10).
  * MC_ESTATE while a round is pending. */
 int mc_set_join_policy(mc_job *job, int64_t scan_max_samples, int passes_before_scan, int passes_without_scan);
+
+/* Length of the checkpoint segments the joint replays (performance only:
+ * every length gives the serial rule's result).  Generation stores each
+ * chain's lattice every C sweeps; every replay of the joint (Sec. 2 step 4:
+ * the search for a chain's first accepted sample, the summary of its
+ * levels, the count of its discarded prefix) runs one segment per GPU lane,
+ * so the segment length bounds the joint's critical path.  The library
+ * aims at segments of about `samples` attempts (whole sweeps; 0 restores
+ * the default of 2^16), keeps at least min(32, S) segments and at most
+ * 2^24 samples per segment, and takes fewer, longer segments where their
+ * checkpoints would exceed 4 GiB.  mc_get_info reports the choice of the
+ * last round.  MC_EINVAL for samples < 0, MC_ESTATE while a round is
+ * pending. */
+int mc_set_segment_samples(mc_job *job, int64_t samples);
 
 /* Checkpoint / resume (no counterpart in the paper).  mc_save writes the
  * job's whole resumable state -- L, n_chains, seed, start, join order,

@@ -21,6 +21,7 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_get_table", "mc_get_spins", "mc_set_spins", "mc_get_energies", "mc_get_trace",
     "mc_get_trace_chain", "mc_get_visited", "mc_set_visited", "mc_thermo", "mc_set_join_order",
     "mc_get_order", "mc_save", "mc_load", "mc_iteration", "mc_set_join_policy", "mc_run_attempts",
+    "mc_set_segment_samples",
     "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error",
     "mc_generate_noalloc", "mc_autotune", "mc_batch_run",
     "mc_job_device_bytes", "mc_server_create", "mc_server_submit", "mc_server_poll", "mc_server_wait",
@@ -51,7 +52,8 @@ class mc_info(ctypes.Structure):
                 ("last_searched", ctypes.c_int64), ("total_joined", ctypes.c_int64),
                 ("placement", ctypes.c_int),
                 ("chains_per_warp", ctypes.c_int), ("warps_per_block", ctypes.c_int),
-                ("device_bytes", ctypes.c_size_t), ("last_scanned", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_size_t), ("last_scanned", ctypes.c_int64),
+                ("segments", ctypes.c_int), ("segment_sweeps", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -118,6 +120,7 @@ def lib():
             "mc_thermo": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
             "mc_set_join_order": (ctypes.c_int, [_vp, ctypes.c_int]),
             "mc_set_join_policy": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int]),
+            "mc_set_segment_samples": (ctypes.c_int, [_vp, ctypes.c_int64]),
             "mc_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
             "mc_iteration": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                             _i64p, ctypes.POINTER(ctypes.c_int)]),
@@ -292,6 +295,10 @@ def mc_load(path: str):
 def mc_set_join_policy(job, scan_max_samples: int = -1, passes_before_scan: int = 2,
                        passes_without_scan: int = 10):
     _check(lib().mc_set_join_policy(job, scan_max_samples, passes_before_scan, passes_without_scan))
+
+
+def mc_set_segment_samples(job, samples: int):
+    _check(lib().mc_set_segment_samples(job, int(samples)))
 
 
 def mc_set_join_order(job, mode: int):
@@ -475,6 +482,9 @@ class Job:
 
     def set_join_order(self, mode: int):
         mc_set_join_order(self.h, mode)
+
+    def set_segment_samples(self, samples: int):
+        mc_set_segment_samples(self.h, samples)
 
     @property
     def order(self):

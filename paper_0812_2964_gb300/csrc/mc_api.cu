@@ -66,6 +66,7 @@ struct mc_job {
   bool trace_valid = false;
   size_t trace_cap = 0;  // int32 elements
   LaunchShape shape;
+  int64_t seg_samples = 0;  // target samples per checkpoint segment (0: default)
   size_t bytes = 0;
   std::vector<void*> allocs;
 };
@@ -101,7 +102,6 @@ void free_all(mc_job* j) {
     for (void* v : j->allocs) raw_free(j, v);
     raw_free(j, j->d.ckpt);
     raw_free(j, j->d.ckm);
-    raw_free(j, j->d.first);
     raw_free(j, j->d.plist);
     raw_free(j, j->d.trace);
   }
@@ -109,7 +109,6 @@ void free_all(mc_job* j) {
   j->d.plist = nullptr;
   j->d.ckpt = nullptr;
   j->d.ckm = nullptr;
-  j->d.first = nullptr;
   j->d.trace = nullptr;
   if (j->own_stream) cudaStreamDestroy(j->own_stream);
   j->own_stream = nullptr;
@@ -196,7 +195,7 @@ static int mc_init_impl(int L, int n_chains, uint64_t seed, int start, mc_job** 
       (rc = dalloc(j, &d.offsets, n_chains)) || (rc = dalloc(j, &d.work, n_chains)) ||
       (rc = dalloc(j, &d.work2, n_chains)) ||
       (rc = dalloc(j, &d.lastacc, n_chains)) || (rc = dalloc(j, &d.summ, 3ull * n_chains)) || (rc = dalloc(j, &d.visited, np1)) ||
-      (rc = dalloc(j, &d.perm, n_chains)) || (rc = dalloc(j, &d.lvcnt, np1)) ||
+      (rc = dalloc(j, &d.perm, n_chains)) || (rc = dalloc(j, &d.lvcnt, np1)) || (rc = dalloc(j, &d.kmin, n_chains)) ||
       (rc = dalloc(j, &d.stats, mcgpu::kStatCount))) {
     free_all(j);
     delete j;
@@ -272,23 +271,36 @@ int mc_set_launch_shape(mc_job* job, int placement, int cpw, int wpb) {
 
 namespace {
 
-// Segments of a round for the joint's parallel replays: at least 32 (or S),
-// and at most 2^24 samples each (the prefix pass relies on that bound).
-void round_segments(int N, int64_t n_sweeps, int* K, int* C) {
-  const int64_t M = n_sweeps * N;
-  int64_t k = std::max<int64_t>(32, (M + (int64_t(1) << 24) - 1) >> 24);
-  k = std::min<int64_t>(k, n_sweeps);
-  const int64_t c = (n_sweeps + k - 1) / k;
+// Segments of a round for the joint's parallel replays.  Every replay of
+// the joint (search, summary, discarded prefixes) runs one segment per lane,
+// so the segment length bounds the joint's critical path: segments of about
+// `target` samples (whole sweeps), at least 32 of them (or S), at most 2^24
+// samples each (the prefix pass relies on that bound), and no more segments
+// than kCheckpointBytes of checkpoints allow.
+constexpr int64_t kSegmentSamples = int64_t(1) << 16;   // default target
+constexpr int64_t kCheckpointBytes = int64_t(4) << 30;   // per job
+
+// Bytes of the checkpoint buffers per segment: lattices, levels, prefix work list.
+size_t bytes_per_segment(int L, int p) {
+  const size_t lw = static_cast<size_t>(L) * ((L + 31) / 32);
+  return static_cast<size_t>(p) * (lw * 4 + 4 + 8);
+}
+
+void round_segments(int L, int p, int64_t n_sweeps, int64_t target, int* K, int* C) {
+  const int64_t N = static_cast<int64_t>(L) * L;
+  if (target <= 0) target = kSegmentSamples;
+  int64_t c = std::max<int64_t>(1, target / N);                      // sweeps per segment
+  const int64_t kmem = std::max<int64_t>(1, kCheckpointBytes / static_cast<int64_t>(bytes_per_segment(L, p)));
+  if ((n_sweeps + c - 1) / c > kmem) c = (n_sweeps + kmem - 1) / kmem;  // fewer, longer segments
+  const int64_t kmin = std::min<int64_t>(32, n_sweeps);
+  if ((n_sweeps + c - 1) / c < kmin) c = (n_sweeps + kmin - 1) / kmin; // enough segments to spread
+  c = std::min<int64_t>(c, std::max<int64_t>(1, (int64_t(1) << 24) / N));
   *C = static_cast<int>(c);
   *K = static_cast<int>((n_sweeps + c - 1) / c);
 }
 
-// Bytes of the checkpoint buffers for K segments: lattices, levels, first
-// accepted sample per segment, prefix work list.
-size_t segment_bytes(const mc_job* job, int K) {
-  const size_t lw = static_cast<size_t>(job->L) * job->wd;
-  return static_cast<size_t>(K) * job->p * (lw * 4 + 4 + 8 + 8);
-}
+// Bytes of the checkpoint buffers for K segments.
+size_t segment_bytes(const mc_job* job, int K) { return static_cast<size_t>(K) * bytes_per_segment(job->L, job->p); }
 
 // Checkpoint buffers for at least K segments.
 int ensure_segments(mc_job* job, int K) {
@@ -299,30 +311,25 @@ int ensure_segments(mc_job* job, int K) {
   if (d.ckpt) {
     raw_free(job, d.ckpt);
     raw_free(job, d.ckm);
-    raw_free(job, d.first);
     raw_free(job, d.plist);
     job->bytes -= segment_bytes(job, d.kcap);
     d.ckpt = nullptr;
     d.ckm = nullptr;
-    d.first = nullptr;
     d.plist = nullptr;
     d.kcap = 0;
   }
-  void *a = nullptr, *b = nullptr, *c = nullptr, *w = nullptr;
+  void *a = nullptr, *b = nullptr, *w = nullptr;
   cudaError_t e = raw_alloc(job, &a, static_cast<size_t>(K) * lw * p * 4);
   if (e == cudaSuccess) e = raw_alloc(job, &b, static_cast<size_t>(K) * p * 4);
-  if (e == cudaSuccess) e = raw_alloc(job, &c, static_cast<size_t>(K) * p * 8);
   if (e == cudaSuccess) e = raw_alloc(job, &w, static_cast<size_t>(K) * p * 8);
   if (e != cudaSuccess) {
     raw_free(job, a);
     raw_free(job, b);
-    raw_free(job, c);
     raw_free(job, w);
     return cuda_fail(e, "checkpoint allocation");
   }
   d.ckpt = static_cast<uint32_t*>(a);
   d.ckm = static_cast<int32_t*>(b);
-  d.first = static_cast<int64_t*>(c);
   d.plist = static_cast<int2*>(w);
   d.kcap = K;
   job->bytes += segment_bytes(job, K);
@@ -359,7 +366,7 @@ int round_prepare(mc_job* job, int64_t n_sweeps, uint64_t* t0) {
   if (job->trace_on)
     if (int rc = ensure_trace(job, n_sweeps)) return rc;
   int K = 0, C = 0;
-  round_segments(job->N, n_sweeps, &K, &C);
+  round_segments(job->L, job->p, n_sweeps, job->seg_samples, &K, &C);
   if (int rc = ensure_segments(job, K)) return rc;
   DevJob& d = job->d;
   d.ck_K = K;
@@ -554,7 +561,7 @@ static int mc_batch_run_impl(mc_job** jobs, int n_jobs, int iterations, int64_t 
   for (int i = 0; i < n_jobs && rc == MC_OK; ++i) {  // no allocation inside a capture
     if (jobs[i]->trace_on) rc = ensure_trace(jobs[i], n_sweeps);
     int K = 0, C = 0;
-    round_segments(jobs[i]->N, n_sweeps, &K, &C);
+    round_segments(jobs[i]->L, jobs[i]->p, n_sweeps, jobs[i]->seg_samples, &K, &C);
     if (rc == MC_OK) rc = ensure_segments(jobs[i], K);
   }
   bool capturing = false;
@@ -818,6 +825,14 @@ int mc_set_join_policy(mc_job* job, int64_t scan_max_samples, int passes_before_
   return MC_OK;
 }
 
+int mc_set_segment_samples(mc_job* job, int64_t samples) {
+  if (int rc = check_job(job)) return rc;
+  if (samples < 0) return fail(MC_EINVAL, "segment samples %lld < 0", static_cast<long long>(samples));
+  if (job->pending) return fail(MC_ESTATE, "round pending");
+  job->seg_samples = samples;
+  return MC_OK;
+}
+
 int mc_set_join_order(mc_job* job, int mode) {
   if (int rc = check_job(job)) return rc;
   if (mode != 0 && mode != 1) return fail(MC_EINVAL, "join order %d: 0 chain index, 1 ascending final energy", mode);
@@ -958,6 +973,8 @@ int mc_get_info(mc_job* job, mc_info* info) {
   info->warps_per_block = job->shape.wpb;
   info->device_bytes = job->bytes;
   info->last_scanned = st[mcgpu::kStatScanned];
+  info->segments = job->d.ck_K;
+  info->segment_sweeps = job->d.ck_C;
   return MC_OK;
 }
 
@@ -1075,12 +1092,13 @@ uint64_t mc_job_device_bytes(int L, int n_chains, int64_t sweeps) {
   const uint64_t N = static_cast<uint64_t>(L) * L, np1 = N + 1, wd = (L + 31) / 32;
   const uint64_t p = static_cast<uint64_t>(n_chains), lw = static_cast<uint64_t>(L) * wd, lat = p * lw;
   // as allocated by mc_init: spins, spins0, m, m0, W, T, h, hgen, dpre, k,
-  // xused, tj, offsets, work, work2, lastacc, summ, visited, perm, lvcnt, stats
+  // xused, tj, offsets, work, work2, lastacc, summ, visited, perm, lvcnt, kmin, stats
   uint64_t b = lat * 4 * 2 + p * 4 * 2 + np1 * 8 + 5 * np1 * 4 + np1 * 8 * 3 + p * 8 + p * 4 + p * np1 * 4 +
-               p * 8 + p * 4 + p * 4 + p * 4 + p * 12 + np1 + p * 4 + np1 * 4 + mcgpu::kStatCount * 8;
+               p * 8 + p * 4 + p * 4 + p * 4 + p * 12 + np1 + p * 4 + np1 * 4 + p * 8 + mcgpu::kStatCount * 8;
   int K = 0, C = 0;
-  round_segments(L * L, sweeps, &K, &C);
-  return b + static_cast<uint64_t>(K) * p * (lw * 4 + 4 + 8 + 8);
+  round_segments(L, n_chains, sweeps, 0, &K, &C);
+  (void)lw;
+  return b + static_cast<uint64_t>(K) * bytes_per_segment(L, n_chains);
 }
 
 int mc_sync(mc_job* job) {

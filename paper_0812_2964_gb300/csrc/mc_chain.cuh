@@ -290,18 +290,28 @@ __device__ __forceinline__ void joint_fill(uint32_t (&U)[32], const int nb, cons
 // first k that passes is recorded.  The test does not steer control flow
 // (the threshold load would then stall every sample): hits are folded into
 // `found` branch-free and the replay loop looks at `done` once per row.
+// poll() (once per sweep) ends the search early when another search has
+// already found an accepted sample of the same chain at or before `stop`
+// (the chain's earliest hit so far, *kmin; nullptr: never).
 struct SearchHook {
   const uint32_t* __restrict__ tj;  // thresholds for moves x -> m, indexed by m
   int64_t k, M, found;
   uint32_t chain, r, k0, k1;
   uint32_t uj[32];
   bool done;
+  const unsigned long long* kmin = nullptr;
+  unsigned long long stop = 0;
   __device__ __forceinline__ void word(int nb) { joint_fill(uj, nb, k, r, chain, k0, k1); }
   __device__ __forceinline__ void sample(int m4, int b) {
     ++k;
     const bool hit = (uj[b] <= __ldg(&tj[m4 >> 2])) && !done && k <= M;
     found = hit ? k : found;
     done = done || hit;
+  }
+  __device__ __forceinline__ void poll() {
+#ifdef __CUDACC__
+    if (kmin && __ldcg(kmin) <= stop) done = true;
+#endif
   }
 };
 
@@ -318,6 +328,7 @@ struct SummaryHook {
   uint32_t run_min;
   bool flag;
   bool done;       // never set: the whole segment is summarised
+  __device__ __forceinline__ void poll() {}
   __device__ __forceinline__ void word(int nb) { joint_fill(uj, nb, k, r, chain, k0, k1); }
   __device__ __forceinline__ void sample(int m4, int b) {
     const int m = m4 >> 2;

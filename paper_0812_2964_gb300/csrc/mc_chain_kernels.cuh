@@ -280,21 +280,27 @@ __device__ __forceinline__ void replay_segment(const DevJob& j, const BlockCtx& 
   Prefetch pf;
   prefetch_init<decltype(run)::WD>(pf, j.L, t0 + static_cast<uint64_t>(s0) * j.N, static_cast<uint32_t>(i), j.key0,
                                    j.key1);
-  for (int64_t s = s0; s < s1 && !hk.done; ++s)
+  for (int64_t s = s0; s < s1 && !hk.done; ++s) {
     run.template sweep<true>(m, pf, b.T, j.np1, static_cast<uint32_t>(i), j.key0, j.key1, hk);
+    hk.poll();
+  }
 }
 
 // Joint search (step 4) over segments [seg_lo, seg_hi): work item (chain,
 // segment) finds the first sample inside the segment that passes the
-// Metropolis test against the chain's input level (0 if none).  The chains
-// are all of them (list_mode 0), work[] (1, a resolution pass) or work2[]
-// (2, those without a hit in segment 0).  Persistent: each warp takes the
-// next cpw consecutive items (segment-major: one segment of consecutive
-// chains) from a global counter, its lanes replay them side by side, and
-// only then takes more, so a long replay holds up one warp, not a wave of
-// blocks.  A segment is skipped when an earlier segment of its chain has
-// already found an accepted sample (first[] is -1 until written).  A block
-// that starts after the queue ran dry leaves before any set-up.
+// Metropolis test against the chain's input level and lowers the chain's
+// kmin to it.  The chains are all of them (list_mode 0), work[] (1, a
+// resolution pass) or work2[] (2, those without a hit in segment 0).
+// Persistent: each warp takes the next cpw consecutive items (segment-major:
+// one segment of consecutive chains) from a global counter, its lanes replay
+// them side by side, and only then takes more, so a long replay holds up one
+// warp, not a wave of blocks.  A segment is skipped, or its replay stopped
+// at the next sweep, as soon as an earlier segment of its chain has found an
+// accepted sample (kmin at or before the segment's start): so the items in
+// flight are always early segments of the chains still without a hit, and
+// as chains find theirs the rest of the GPU moves on to the others' later
+// segments.  A block that starts after the queue ran dry leaves before any
+// set-up.
 template <class Factory, bool TSMEM>
 __global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int cpw, const uint64_t t0,
                                                      const int64_t S, const uint32_t r, const int list_mode,
@@ -323,10 +329,8 @@ __global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int c
       const int seg = seg_lo + static_cast<int>(item / nchains);
       const int q = static_cast<int>(item % nchains);
       const int i = list_mode ? list[q] : q;
-      int64_t* fi = j.first + static_cast<size_t>(i) * j.kcap;
-      bool earlier = false;
-      for (int s2 = 0; s2 < seg && !earlier; ++s2) earlier = __ldcg(&fi[s2]) > 0;
-      if (!earlier) {
+      const unsigned long long seg_start = static_cast<unsigned long long>(seg) * j.ck_C * j.N;
+      if (__ldcg(&j.kmin[i]) > seg_start) {   // no accepted sample before this segment yet
         const int x = j.xused[i];
         int64_t found;
         if (x < 0) {
@@ -334,7 +338,7 @@ __global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int c
         } else {
           SearchHook hk;
           hk.tj = j.tj + static_cast<size_t>(i) * j.np1;
-          hk.k = static_cast<int64_t>(seg) * j.ck_C * j.N;
+          hk.k = static_cast<int64_t>(seg_start);
           hk.M = min(S, static_cast<int64_t>(seg + 1) * j.ck_C) * j.N;
           hk.found = 0;
           hk.chain = static_cast<uint32_t>(i);
@@ -342,12 +346,14 @@ __global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int c
           hk.k0 = j.key0;
           hk.k1 = j.key1;
           hk.done = false;
+          hk.kmin = &j.kmin[i];
+          hk.stop = seg_start;
           const int64_t k_begin = hk.k;
           replay_segment<Factory>(j, b, i, seg, t0, S, hk);
           found = hk.found;
           searched += hk.k - k_begin;
         }
-        fi[seg] = found;
+        if (found > 0) atomicMin(&j.kmin[i], static_cast<unsigned long long>(found));
       }
     }
     __syncwarp();
@@ -412,6 +418,7 @@ struct PrefixHook {
   uint32_t* hist;
   int64_t k, cut;  // samples with index < cut are counted
   bool done;
+  __device__ __forceinline__ void poll() {}
   __device__ __forceinline__ void word(int) {}
   __device__ __forceinline__ void sample(int m4, int) {
     if (done) return;

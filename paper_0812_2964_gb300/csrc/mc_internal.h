@@ -42,7 +42,7 @@ struct DevJob {
   int32_t* trace;      // [S][p] energy after each sweep (nullable)
   uint32_t* ckpt;      // [kcap][L*wd][p] lattice at the start of each round segment
   int32_t* ckm;        // [kcap][p] level at the start of each round segment
-  int64_t* first;      // [p][kcap] first accepted sample inside each segment (0: none)
+  unsigned long long* kmin;  // [p] earliest accepted sample found so far for the chain's input (kNoHit: none)
   int2* plist;         // [p*kcap] (chain, segment) work list of the prefix pass
   int32_t* summ;       // [3][p] summary pass: lowest and highest level visited, flag
   uint8_t* visited;    // [np1] 1 once a weight update has seen h > 0 at the level
@@ -58,6 +58,9 @@ struct DevJob {
   int kcap;            // segment capacity
   long long* stats;    // [kStatCount] small device counters
 };
+
+// kmin[] value of a chain with no accepted sample found (yet)
+constexpr unsigned long long kNoHit = 0x7FFFFFFFFFFFFFFFull;
 
 enum StatIndex : int {
   kStatCarry = 0,        // level passed on to the next round's chain 0

@@ -329,11 +329,8 @@ __global__ void clear_stats_kernel(const DevJob j) {
     j.stats[kStatScanned] = 0;
     j.stats[kStatFirstPending] = j.p;
   }
-  // first accepted sample per segment: -1 = not searched yet
-  const long long n = static_cast<long long>(j.p) * j.kcap;
-  for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < n;
-       idx += static_cast<long long>(gridDim.x) * blockDim.x)
-    j.first[idx] = -1;
+  // earliest accepted sample of each chain: none found yet
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < j.p; i += gridDim.x * blockDim.x) j.kmin[i] = kNoHit;
 }
 
 // One grid-wide resolution pass, part 1 (one block): with the current k's,
@@ -370,7 +367,7 @@ __global__ void __launch_bounds__(1024) mark_kernel(const DevJob j, const int de
     if (x != j.xused[i]) {
       j.xused[i] = x;
       j.k[i] = -1;
-      for (int s2 = 0; s2 < j.ck_K; ++s2) j.first[static_cast<size_t>(i) * j.kcap + s2] = -1;
+      j.kmin[i] = kNoHit;
       j.work[atomicAdd(&s_count, 1)] = i;
       atomicMin(&s_first, q);
       atomicAdd(&s_new, 1);
@@ -492,8 +489,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const DevJob j) {
             j.k[ch] = 0;
           }
         }
-        if (acc && x >= 0)
-          for (int s2 = t; s2 < j.ck_K; s2 += nt) j.first[static_cast<size_t>(ch) * j.kcap + s2] = -1;
+        if (acc && x >= 0 && t == 0) j.kmin[ch] = kNoHit;
       }
       if (acc) x = s_m[q];
     }
@@ -527,9 +523,10 @@ __global__ void __launch_bounds__(1024) nohit_kernel(const DevJob j, const int l
   if (threadIdx.x == 0) s_count = 0;
   __syncthreads();
   const int n = list_mode ? static_cast<int>(j.stats[kStatPending]) : j.p;
+  const unsigned long long segN = static_cast<unsigned long long>(j.ck_C) * static_cast<unsigned long long>(j.N);
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
     const int i = list_mode ? j.work[q] : q;
-    if (j.first[static_cast<size_t>(i) * j.kcap] == 0) j.work2[atomicAdd(&s_count, 1)] = i;
+    if (j.kmin[i] > segN) j.work2[atomicAdd(&s_count, 1)] = i;
   }
   __syncthreads();
   if (threadIdx.x == 0) j.stats[kStatNoHit] = s_count;
@@ -737,20 +734,14 @@ cudaError_t join_prelude(const DevJob& j, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// k_i = the first accepted sample of the first segment that has one (0: none).
+// k_i = the earliest accepted sample the search found (0: none).
 __global__ void select_kernel(const DevJob j, const int listed) {
   const int n = listed ? static_cast<int>(j.stats[kStatPending]) : j.p;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const int i = listed ? j.work[q] : q;
-  const int64_t* f = j.first + static_cast<size_t>(i) * j.kcap;
-  int64_t k = 0;
-  for (int s = 0; s < j.ck_K; ++s)
-    if (f[s] > 0) {
-      k = f[s];
-      break;
-    }
-  j.k[i] = k;
+  const unsigned long long k = j.kmin[i];
+  j.k[i] = k == kNoHit ? 0 : static_cast<int64_t>(k);
 }
 
 // Work list of the prefix pass: for every chain, its whole segments before

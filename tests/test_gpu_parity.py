@@ -36,11 +36,14 @@ def _compare_weights(g, o):
     assert np.array_equal(g.visited, o.visited)
 
 
-def _run_parity(L, p, S, iters, start, seed, weights=None, shape=None, M_total=0, order=0, policy=None):
+def _run_parity(L, p, S, iters, start, seed, weights=None, shape=None, M_total=0, order=0, policy=None,
+                seg=None):
     N = L * L
     g = mc.Job(L, p, seed, start)
     if policy is not None:
         g.set_join_policy(*policy)
+    if seg is not None:
+        g.set_segment_samples(seg)
     if shape is not None:
         g.set_launch_shape(*shape)
     g.set_trace(True)
@@ -133,6 +136,39 @@ def test_every_resolution_path_gives_the_serial_rule(policy, L, p, S):
     W = random_weights(L, seed=L + 9, scale=10.0)
     g, o, mism = _run_parity(L, p, S, 3, 1, seed=900 + L, weights=W, policy=policy)
     assert mism > 0
+
+
+@pytest.mark.parametrize("L,p,S,seg,K,C", [
+    (8, 40, 200, 64 * 3, 67, 3),     # multi-sweep segments, many of them
+    (8, 40, 200, 1, 200, 1),         # one sweep each
+    (16, 64, 96, 256, 96, 1),
+    (32, 70, 64, 1024, 64, 1),
+    (16, 64, 60, 256 * 7, 30, 2),    # too few at 7 sweeps: at least 32 (here 30 of 2)
+])
+def test_segment_lengths_give_the_serial_rule(L, p, S, seg, K, C):
+    # the joint's replays run one checkpoint segment per lane; with rough
+    # weights the first accepted samples fall in late segments of their
+    # chains, where the search skips and stops segments behind an earlier hit
+    W = random_weights(L, seed=L + 21, scale=10.0)
+    g, o, mism = _run_parity(L, p, S, 2, 1, seed=300 + L, weights=W, seg=seg)
+    info = g.info()
+    assert (info["segments"], info["segment_sweeps"]) == (K, C)
+    k = g.k
+    M = S * L * L
+    assert ((k > C * L * L) & (k <= M)).any()      # some hits beyond the first segment
+
+
+def test_segment_length_argument_checks():
+    g = mc.Job(8, 4, 1, 1)
+    with pytest.raises(mc.McError) as e:
+        g.set_segment_samples(-1)
+    assert e.value.code == mc.MC_EINVAL
+    g.run_sweeps(1)
+    with pytest.raises(mc.McError) as e:
+        g.set_segment_samples(100)
+    assert e.value.code == mc.MC_ESTATE
+    g.join()
+    g.set_segment_samples(0)
 
 
 def test_naive_join_matches_oracle():
