@@ -193,6 +193,176 @@ def run_reference(args):
     return 0
 
 
+def timed_iterations(torch, job, stream, S, steps, flush):
+    """`steps` weight iterations of one job (round of S sweeps, joint, weight
+    update, L2 flush), timed with CUDA events on the job's stream: total
+    seconds, mean milliseconds per phase, generation milliseconds per step."""
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    # per step: events before generation, the joint, the weight update and the L2 flush
+    marks = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for i in range(steps):
+            e = marks[i]
+            e[0].record(stream)
+            job.run_sweeps(S)              # generation kernel (+ round-start copy)
+            e[1].record(stream)
+            job.join(want_length=False)    # joint: search, resolution, correction, scan
+            e[2].record(stream)
+            job.update_weights()           # Eq. (new_weight) + threshold table
+            e[3].record(stream)
+            flush.fill_(1)                 # L2 flushed between timed steps
+            e[4].record(stream)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    gen_ms = [e[0].elapsed_time(e[1]) for e in marks]
+    phases = {name: statistics.mean(e[a].elapsed_time(e[a + 1]) for e in marks)
+              for a, name in enumerate(("gen_ms", "joint_ms", "update_ms", "l2_flush_ms"))}
+    phases["joint_ms_max"] = max(e[1].elapsed_time(e[2]) for e in marks)
+    return ev0.elapsed_time(ev1) / 1e3, phases, gen_ms
+
+
+def alu_roofline(p, S, N, gen_ms):
+    """Algorithmic integer operations of one generation launch per second of
+    its mean CUDA-event time, against the integer-issue peak."""
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    peak_ops = SMS * SUBPARTITIONS * LANES * sm_max * 1e6
+    achieved = p * S * N * ALG_OPS_PER_ATTEMPT / (statistics.mean(gen_ms) / 1e3)
+    return {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
+            "frac": achieved / peak_ops, "kernel_ms": statistics.mean(gen_ms), "ops_per_attempt": ALG_OPS_PER_ATTEMPT,
+            "peak_source": f"{SMS} SMs x {SUBPARTITIONS} sub-partitions x {LANES} lanes x "
+                           f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"}
+
+
+# reduced sizes of the other workloads measured beside the headline (one line)
+SUB = dict(L64_sweeps=2000, L128_sweeps=400, job_steps=3, job_warmup=3,
+           batch_sweeps=5000, batch_steps=2, batch_warmup=1,
+           serving_jobs=60, serving_rate=20.0, serving_sweeps=20, serving_slots=64)
+
+
+def job_record(torch, mc, device, workload, S, steps, warmup):
+    """One job of `workload` at S sweeps per iteration (the workload's L, chains,
+    seed and start), device-timed like the headline."""
+    w = WORKLOADS[workload]
+    t_wall = time.perf_counter()
+    stream = torch.cuda.Stream(device=device)
+    job = mc.Job(w.L, w.chains, w.seed, w.start)
+    job.set_stream(stream.cuda_stream)
+    job.set_trace(True)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            job.run_sweeps(S)
+            job.join(want_length=False)
+            job.update_weights()
+    torch.cuda.synchronize()
+    kept0 = job.info()["total_joined"]
+    el, phases, gen_ms = timed_iterations(torch, job, stream, S, steps, flush)
+    info = job.info()
+    kept = info["total_joined"] - kept0
+    M = S * w.N
+    rec = {"metric": METRIC, "value": kept / el, "unit": UNIT,
+           "config": {"workload": workload, "L": w.L, "chains": w.chains, "sweeps_per_iteration": S,
+                      "sweeps_of_the_workload": w.sweeps, "seed": w.seed,
+                      "weight_iterations_timed": f"{warmup + 1}..{warmup + steps}",
+                      "launch": {"placement": ["registers", "shared"][info["placement"]],
+                                 "chains_per_warp": info["chains_per_warp"],
+                                 "warps_per_block": info["warps_per_block"]}},
+           "ms_per_step": 1e3 * el / steps, "kept_fraction": kept / (steps * w.chains * M),
+           "raw_attempts_per_s": steps * w.chains * M / el, "phases": phases,
+           "roofline": alu_roofline(w.chains, S, w.N, gen_ms),
+           "timing": "CUDA events on the job's stream"}
+    job.close()
+    rec["wall_s"] = time.perf_counter() - t_wall
+    return rec
+
+
+def batch_record(torch, mc, S, steps, warmup, tune, rank=0):
+    """The uneven batch run three ways on the same chains; kept samples/s of each."""
+    from paper_0812_2964_gb300.workloads import BATCH_GROUPS
+
+    modes = {0: "one launch per job", 1: "one fused launch", 2: "fused launch, CUDA graph"}
+    out = {}
+    t_wall = time.perf_counter()
+    for mode in (0, 1, 2):
+        jobs = [mc.Job(L, p, seed + rank, 1) for (L, p, seed) in BATCH_GROUPS]
+        for j in jobs:
+            j.set_trace(True)
+            if tune:
+                j.autotune(probe_sweeps=max(1, min(S, 2_000_000 // j.N)))
+        mc.mc_batch_run(jobs, warmup, S, mode)
+        torch.cuda.synchronize()
+        kept0 = sum(j.info()["total_joined"] for j in jobs)
+        l0 = mc.mc_kernel_launches()
+        t0 = time.perf_counter()
+        mc.mc_batch_run(jobs, steps, S, mode)   # synchronises
+        el = time.perf_counter() - t0
+        launches = mc.mc_kernel_launches() - l0
+        kept = sum(j.info()["total_joined"] for j in jobs) - kept0
+        attempts = sum(j.p * S * j.N for j in jobs) * steps
+        out[mode] = {"mode": modes[mode], "value": kept / el, "seconds": el, "kept": kept,
+                     "raw_attempts_per_s": attempts / el, "gpu_launches": launches,
+                     "shapes": [[j.info()[k] for k in ("placement", "chains_per_warp", "warps_per_block")]
+                                for j in jobs]}
+        for j in jobs:
+            j.close()
+    return {"metric": METRIC, "value": out[2]["value"], "unit": UNIT,
+            "config": {"workload": "batch_uneven", "groups": [list(g) for g in BATCH_GROUPS],
+                       "sweeps_per_iteration": S, "iterations_timed": steps, "autotuned": bool(tune),
+                       "timing": "host wall clock around the synchronising call"},
+            "modes": out, "fused_vs_per_job": out[1]["value"] / out[0]["value"],
+            "graph_vs_per_job": out[2]["value"] / out[0]["value"], "wall_s": time.perf_counter() - t_wall}
+
+
+def serving_record(mc, n_jobs, rate, S, slots, rank=0):
+    """A Poisson stream of weight-estimation jobs submitted at their arrival
+    times to the continuous-batching server (40 GB budget)."""
+    from paper_0812_2964_gb300.workloads import serving_stream
+
+    t_wall = time.perf_counter()
+    stream = serving_stream(n_jobs, rate=rate, sweeps=S)
+    budget = 40 << 30
+    with mc.Server(budget, slots) as srv:     # warm-up: one small job of every size
+        for i, L in enumerate((16, 32, 48, 64, 96, 128)):
+            srv.wait(srv.submit(L, 256, 99 + i, 2, S))
+    l0 = mc.mc_kernel_launches()
+    with mc.Server(budget, slots) as srv:
+        ids = []
+        t_base = srv.clock()
+        for job in stream:
+            delay = t_base + job.arrival - srv.clock()
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(job.L, job.chains, job.seed + rank, job.iterations, job.sweeps))
+        res = [srv.wait(j) for j in ids]
+        info = srv.info()
+    launches = mc.mc_kernel_launches() - l0
+    st = [r[1] for r in res]
+    lat = np.array([s["t_done"] - s["t_submit"] for s in st])
+    qwait = np.array([s["t_admit"] - s["t_submit"] for s in st])
+    span = max(s["t_done"] for s in st) - min(s["t_submit"] for s in st)
+    joined = sum(s["joined"] for s in st)
+    attempts = sum(s["attempts"] for s in st)
+    offered = attempts / max(1e-9, stream[-1].arrival - stream[0].arrival)
+    d2h = sum((j.L * j.L + 1) * 8 for j in stream)
+    return {"metric": METRIC, "value": joined / span, "unit": UNIT,
+            "config": {"workload": "serving", "jobs": len(stream), "rate_jobs_per_s": rate, "arrival_seed": 5,
+                       "sizes": [16, 32, 48, 64, 96, 128], "chains": "256..4096 step 256",
+                       "iterations": "20..60", "sweeps_per_iteration": S, "budget_bytes": budget, "slots": slots,
+                       "step": "one job (arrival to W ready)"},
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(lat.mean()), "max": float(lat.max())},
+            "queue_wait_s": {"p50": float(np.percentile(qwait, 50)), "p99": float(np.percentile(qwait, 99))},
+            "makespan_s": span, "jobs_per_s": len(stream) / span,
+            "raw_attempts_per_s": attempts / span, "offered_attempts_per_s": offered,
+            "utilisation_proxy": offered / (attempts / span),
+            "server": {k: info[k] for k in ("peak_active", "peak_bytes", "admitted", "completed")},
+            "d2h_bytes_per_job": d2h / len(stream), "gpu_launches": launches,
+            "wall_s": time.perf_counter() - t_wall}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -238,33 +408,10 @@ def run_gpu(args):
     clocks.start()
     time.sleep(0.4)
     launches0 = mc.mc_kernel_launches()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    # per step: events before generation, the joint, the weight update and the L2 flush
-    marks = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
-    with torch.cuda.stream(stream):
-        ev0.record(stream)
-        for i in range(args.steps):
-            e = marks[i]
-            e[0].record(stream)
-            job.run_sweeps(S)              # generation kernel (+ round-start copy)
-            e[1].record(stream)
-            job.join(want_length=False)    # joint: search, resolution, correction, scan
-            e[2].record(stream)
-            job.update_weights()           # Eq. (new_weight) + threshold table
-            e[3].record(stream)
-            flush.fill_(1)                 # L2 flushed between timed steps
-            e[4].record(stream)
-        ev1.record(stream)
-    torch.cuda.synchronize()
+    elapsed, phases, gen_ms = timed_iterations(torch, job, stream, S, args.steps, flush)
     launches = mc.mc_kernel_launches() - launches0
     clk = clocks.stop()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
     kept = job.info()["total_joined"] - kept0
-    gen_ms = [e[0].elapsed_time(e[1]) for e in marks]
-    phases = {name: statistics.mean(e[a].elapsed_time(e[a + 1]) for e in marks)
-              for a, name in enumerate(("gen_ms", "joint_ms", "update_ms", "l2_flush_ms"))}
-    phases["joint_ms_max"] = max(e[1].elapsed_time(e[2]) for e in marks)
     info = job.info()
     if world > 1:
         dist.barrier()
@@ -304,12 +451,7 @@ def run_gpu(args):
         return 0
 
     # ---- roofline of the dominant kernel (generation)
-    peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
-    peak_ops = SMS * SUBPARTITIONS * LANES * sm_max * 1e6
-    gen_s = statistics.mean(gen_ms) / 1e3
-    gen_attempts = p * M
-    achieved = gen_attempts * ALG_OPS_PER_ATTEMPT / gen_s
+    roof = alu_roofline(p, S, N, gen_ms)
     tr = _traffic_record()
     same_kernel = tr.get("workload") == args.workload and tr.get("kernel_rev") == mc.KERNEL_REV
     traffic = None
@@ -342,18 +484,13 @@ def run_gpu(args):
         "phases": phases,
         "kept_fraction": kept / (args.steps * p * M),
         "raw_attempts_per_s": args.steps * p * M * world / t_max,
-        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
-                     "unit": "Gop/s", "frac": achieved / peak_ops, "traffic": traffic,
+        "roofline": {**roof, "traffic": traffic,
                      "kernel": "gen_kernel (lattice rows in %s)" % ["registers", "shared memory"][info["placement"]],
-                     "kernel_ms": statistics.mean(gen_ms),
-                     "ops_per_attempt": ALG_OPS_PER_ATTEMPT,
                      "measured_issue_active": (issue / 100.0) if issue is not None else None,
                      "measured_issue_lane_weighted": (issue / 100.0 * tr.get("lanes_active", 32) / 32)
                      if issue is not None else None,
                      "measured_issue_source": tr.get("issue_active_source") if issue is not None else None,
-                     "traffic_source": tr.get("traffic_source") if traffic is not None else None,
-                     "peak_source": f"{SMS} SMs x {SUBPARTITIONS} sub-partitions x {LANES} lanes x "
-                                    f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"},
+                     "traffic_source": tr.get("traffic_source") if traffic is not None else None},
         "e2e": {"value": e2e_all / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "gpu_launches": launches,
@@ -363,6 +500,20 @@ def run_gpu(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if world == 1 and not args.no_subrecords and args.workload == WORKLOAD:
+        # the rest of the metric, at reduced sizes named in each record's config
+        del job, flush
+        torch.cuda.empty_cache()
+        line["subrecords"] = {
+            "L64_p4096": job_record(torch, mc, device, "L64_p4096", SUB["L64_sweeps"], SUB["job_steps"],
+                                    SUB["job_warmup"]),
+            "L128_p1024": job_record(torch, mc, device, "L128_p1024", SUB["L128_sweeps"], SUB["job_steps"],
+                                     SUB["job_warmup"]),
+            "batch_uneven": batch_record(torch, mc, SUB["batch_sweeps"], SUB["batch_steps"], SUB["batch_warmup"],
+                                         args.tune),
+            "serving": serving_record(mc, SUB["serving_jobs"], SUB["serving_rate"], SUB["serving_sweeps"],
+                                      SUB["serving_slots"]),
+        }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -377,50 +528,21 @@ def run_batch(args):
     import torch
 
     import paper_0812_2964_gb300 as mc
-    from paper_0812_2964_gb300.workloads import BATCH_GROUPS
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     mc.build()
     S = args.sweeps or 50_000
-    modes = {0: "one launch per job", 1: "one fused launch", 2: "fused launch, CUDA graph"}
-    out = {}
-    for mode in (0, 1, 2):
-        jobs = [mc.Job(L, p, seed + rank, 1) for (L, p, seed) in BATCH_GROUPS]
-        for j in jobs:
-            j.set_trace(True)
-            if args.tune:
-                j.autotune(probe_sweeps=max(1, min(S, 2_000_000 // j.N)))
-        mc.mc_batch_run(jobs, args.warmup, S, mode)
-        torch.cuda.synchronize()
-        kept0 = sum(j.info()["total_joined"] for j in jobs)
-        clocks = ClockSampler(local)
-        clocks.start()
-        time.sleep(0.3)
-        l0 = mc.mc_kernel_launches()
-        t0 = time.perf_counter()
-        mc.mc_batch_run(jobs, args.steps, S, mode)   # synchronises
-        el = time.perf_counter() - t0
-        launches = mc.mc_kernel_launches() - l0
-        clk = clocks.stop()
-        kept = sum(j.info()["total_joined"] for j in jobs) - kept0
-        attempts = sum(j.p * S * j.N for j in jobs) * args.steps
-        out[mode] = {"mode": modes[mode], "value": kept / el, "seconds": el, "kept": kept,
-                     "raw_attempts_per_s": attempts / el, "gpu_launches": launches, "clocks": clk,
-                     "shapes": [[j.info()[k] for k in ("placement", "chains_per_warp", "warps_per_block")]
-                                for j in jobs]}
-        for j in jobs:
-            j.close()
-    best = out[2]
-    line = {"metric": METRIC, "value": best["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+    clocks = ClockSampler(local)
+    clocks.start()
+    rec = batch_record(torch, mc, S, args.steps, args.warmup, args.tune, rank)
+    clk = clocks.stop()
+    best = rec["modes"][2]
+    line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * best["seconds"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "batch_uneven", "groups": [list(g) for g in BATCH_GROUPS],
-                       "sweeps_per_iteration": S, "timing": "host wall clock around the synchronising call",
-                       "autotuned": bool(args.tune)},
-            "modes": out, "fused_vs_per_job": out[1]["value"] / out[0]["value"],
-            "graph_vs_per_job": out[2]["value"] / out[0]["value"], "clocks": best["clocks"],
-            "gpu_launches": best["gpu_launches"]}
+            "config": rec["config"], "modes": rec["modes"], "fused_vs_per_job": rec["fused_vs_per_job"],
+            "graph_vs_per_job": rec["graph_vs_per_job"], "clocks": clk, "gpu_launches": best["gpu_launches"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -434,61 +556,26 @@ def run_serving(args):
     import torch
 
     import paper_0812_2964_gb300 as mc
-    from paper_0812_2964_gb300.workloads import serving_stream
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     mc.build()
     S = args.sweeps or 20
-    stream = serving_stream(args.jobs, rate=args.rate, sweeps=S)
-    budget = 40 << 30
-    # warm-up: one small job of every size (module load, first launches)
-    with mc.Server(budget, args.slots) as srv:
-        for i, L in enumerate((16, 32, 48, 64, 96, 128)):
-            srv.wait(srv.submit(L, 256, 99 + i, 2, S))
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.3)
-    l0 = mc.mc_kernel_launches()
-    with mc.Server(budget, args.slots) as srv:
-        ids = []
-        t_base = srv.clock()
-        for job in stream:
-            delay = t_base + job.arrival - srv.clock()
-            if delay > 0:
-                time.sleep(delay)
-            ids.append(srv.submit(job.L, job.chains, job.seed + rank, job.iterations, job.sweeps))
-        res = [srv.wait(j) for j in ids]
-        info = srv.info()
-    launches = mc.mc_kernel_launches() - l0
+    rec = serving_record(mc, args.jobs, args.rate, S, args.slots, rank)
     clk = clocks.stop()
-    st = [r[1] for r in res]
-    lat = np.array([s["t_done"] - s["t_submit"] for s in st])
-    qwait = np.array([s["t_admit"] - s["t_submit"] for s in st])
-    t_first = min(s["t_submit"] for s in st)
-    t_last = max(s["t_done"] for s in st)
-    span = t_last - t_first
-    joined = sum(s["joined"] for s in st)
-    attempts = sum(s["attempts"] for s in st)
-    offered = attempts / max(1e-9, stream[-1].arrival - stream[0].arrival)
-    d2h = sum((j.L * j.L + 1) * 8 for j in stream)
-    value = joined / span
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(stream),
-            "warmup": 6, "ms_per_step": 1e3 * span / len(stream), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "serving", "jobs": len(stream), "rate_jobs_per_s": args.rate,
-                       "arrival_seed": 5, "sizes": [16, 32, 48, 64, 96, 128], "chains": "256..4096 step 256",
-                       "iterations": "20..60", "sweeps_per_iteration": S, "budget_bytes": budget,
-                       "slots": args.slots, "step": "one job (arrival to W ready)"},
-            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                          "mean": float(lat.mean()), "max": float(lat.max())},
-            "queue_wait_s": {"p50": float(np.percentile(qwait, 50)), "p99": float(np.percentile(qwait, 99))},
-            "raw_attempts_per_s": attempts / span, "offered_attempts_per_s": offered,
-            "utilisation_proxy": offered / (attempts / span),
-            "server": {k: info[k] for k in ("peak_active", "peak_bytes", "admitted", "completed")},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h / len(stream),
+    n = rec["config"]["jobs"]
+    line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": n,
+            "warmup": 6, "ms_per_step": 1e3 * rec["makespan_s"] / n, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": rec["config"],
+            "latency_s": rec["latency_s"], "queue_wait_s": rec["queue_wait_s"],
+            "raw_attempts_per_s": rec["raw_attempts_per_s"], "offered_attempts_per_s": rec["offered_attempts_per_s"],
+            "utilisation_proxy": rec["utilisation_proxy"], "server": rec["server"],
+            "e2e": {"value": rec["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": rec["d2h_bytes_per_job"],
                     "note": "host-timed from submission to collection; each job's input is its spec"},
-            "gpu_launches": launches, "clocks": clk}
+            "gpu_launches": rec["gpu_launches"], "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -563,6 +650,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-subrecords", action="store_true",
+                    help="skip the reduced-size L=64, L=128, batch and serving records of the default run")
     ap.add_argument("--jobs", type=int, default=400, help="serving: jobs in the arrival stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=64, help="serving: server slots")

@@ -104,11 +104,21 @@ int mc_run_sweeps(mc_job *job, int64_t n_sweeps);
  * continues across rounds.  Whole sweeps from a sweep boundary take the
  * mc_run_sweeps path; any other round (and any mc_run_sweeps while the
  * chains are inside a sweep) runs one thread per chain on its lattice in
- * global memory and is joined by the serial rule itself (meant for short
- * rounds); no trace is recorded for such a round, and mc_batch_run refuses
- * jobs inside a sweep.  1 <= n_attempts < 2^34.  Asynchronous; MC_ESTATE if
- * the previous round has not been joined. */
+ * global memory (meant for short rounds) and records the level of every
+ * sample (p * n_attempts int32, see mc_set_partial_record), from which
+ * mc_join applies the serial rule chain by chain, each chain's samples
+ * tested in parallel; rounds too large to record are joined by replaying
+ * each chain in one thread.  No trace is recorded for such a round, and
+ * mc_batch_run refuses jobs inside a sweep.  1 <= n_attempts < 2^34.
+ * Asynchronous; MC_ESTATE if the previous round has not been joined. */
 int mc_run_attempts(mc_job *job, int64_t n_attempts);
+
+/* Largest record (p * n_attempts entries, int32 each) that a round of
+ * mc_run_attempts keeps for its joint; larger rounds are joined by serial
+ * replay (performance and memory only: both give the serial rule's result).
+ * max_entries < 0 restores the default 2^26.  MC_ESTATE while a round is
+ * pending. */
+int mc_set_partial_record(mc_job *job, int64_t max_entries);
 
 /* Sec. 2 steps 3-5 for the last round: chain i (in order; see
  * mc_set_join_order) keeps its samples from the first one that passes the
@@ -308,6 +318,18 @@ int mc_sync(mc_job *job);
 int mc_generate_noalloc(int L, int n_chains, uint64_t seed, uint64_t t0, int64_t n_sweeps,
                         uint32_t *d_spins, int32_t *d_levels, const double *d_weights,
                         int64_t *d_hist, void *cuda_stream);
+
+/* Failure injection for tests of the error paths (no counterpart in the
+ * paper).  After `after` more device allocations by this library (job state,
+ * checkpoint segments, traces, statistical-average buffers; those a server
+ * makes when it admits a job count too), the next one fails on the host
+ * before any CUDA call, as an out-of-memory would, and the calling entry
+ * point returns MC_ENOMEM after releasing what it had allocated; later
+ * allocations succeed again.  after < 0 disarms it.  Process-wide.
+ * mc_live_allocations: device allocations this library holds right now (a
+ * leak check: it returns to its old value once the jobs are freed). */
+int mc_inject_alloc_failure(int64_t after);
+int64_t mc_live_allocations(void);
 
 /* Number of kernels this library has launched since it was loaded. */
 uint64_t mc_kernel_launches(void);

@@ -21,14 +21,14 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_get_table", "mc_get_spins", "mc_set_spins", "mc_get_energies", "mc_get_trace",
     "mc_get_trace_chain", "mc_get_visited", "mc_set_visited", "mc_thermo", "mc_set_join_order",
     "mc_get_order", "mc_save", "mc_load", "mc_iteration", "mc_set_join_policy", "mc_run_attempts",
-    "mc_set_segment_samples",
+    "mc_set_segment_samples", "mc_set_partial_record", "mc_inject_alloc_failure", "mc_live_allocations",
     "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error",
     "mc_generate_noalloc", "mc_autotune", "mc_batch_run",
     "mc_job_device_bytes", "mc_server_create", "mc_server_submit", "mc_server_poll", "mc_server_wait",
     "mc_server_get_info", "mc_server_clock", "mc_server_free", "Server"]
 
 # revision of the generation kernel; bump when it changes (profiles record it)
-KERNEL_REV = "gen-4"
+KERNEL_REV = "gen-5"
 
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ESTATE, MC_ETIMEOUT = 0, -1, -2, -3, -4, -5
 _NAMES = {MC_EINVAL: "MC_EINVAL", MC_ENOMEM: "MC_ENOMEM", MC_ECUDA: "MC_ECUDA",
@@ -121,6 +121,7 @@ def lib():
             "mc_set_join_order": (ctypes.c_int, [_vp, ctypes.c_int]),
             "mc_set_join_policy": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int]),
             "mc_set_segment_samples": (ctypes.c_int, [_vp, ctypes.c_int64]),
+            "mc_set_partial_record": (ctypes.c_int, [_vp, ctypes.c_int64]),
             "mc_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
             "mc_iteration": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                             _i64p, ctypes.POINTER(ctypes.c_int)]),
@@ -148,6 +149,8 @@ def lib():
             "mc_server_clock": (ctypes.c_double, [_vp]),
             "mc_server_free": (None, [_vp]),
             "mc_kernel_launches": (ctypes.c_uint64, []),
+            "mc_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int64]),
+            "mc_live_allocations": (ctypes.c_int64, []),
             "mc_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -297,6 +300,10 @@ def mc_set_join_policy(job, scan_max_samples: int = -1, passes_before_scan: int 
     _check(lib().mc_set_join_policy(job, scan_max_samples, passes_before_scan, passes_without_scan))
 
 
+def mc_set_partial_record(job, max_entries: int):
+    _check(lib().mc_set_partial_record(job, int(max_entries)))
+
+
 def mc_set_segment_samples(job, samples: int):
     _check(lib().mc_set_segment_samples(job, int(samples)))
 
@@ -364,6 +371,14 @@ def mc_last_error() -> str:
 
 def mc_kernel_launches() -> int:
     return int(lib().mc_kernel_launches())
+
+
+def mc_inject_alloc_failure(after: int):
+    _check(lib().mc_inject_alloc_failure(int(after)))
+
+
+def mc_live_allocations() -> int:
+    return int(lib().mc_live_allocations())
 
 
 # ------------------------------------------------------------ convenience
@@ -485,6 +500,9 @@ class Job:
 
     def set_segment_samples(self, samples: int):
         mc_set_segment_samples(self.h, samples)
+
+    def set_partial_record(self, max_entries: int):
+        mc_set_partial_record(self.h, max_entries)
 
     @property
     def order(self):

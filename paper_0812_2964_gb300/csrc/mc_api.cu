@@ -1,6 +1,7 @@
 // C ABI (include/mc.h): job lifetime, device memory, stream ordering and
 // argument checking around the kernels of mc_kernels.cu.
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -61,6 +62,9 @@ struct mc_job {
   int64_t last_S = 0;
   int64_t last_M = 0;           // attempts per chain of the last round
   bool attempts_round = false;  // the last round was not whole sweeps from a sweep start
+  bool attempts_recorded = false;  // ... and its samples' levels are in d.plv
+  size_t plv_cap = 0;           // int32 entries of d.plv
+  long long plv_max = mcgpu::kPartialLevelsMax;  // largest p * M recorded
   bool pending = false;
   bool trace_on = false;
   bool trace_valid = false;
@@ -77,12 +81,31 @@ namespace {
 // (cudaMallocAsync / cudaFreeAsync on the job's stream): freeing a job does
 // not wait for work of other jobs, which a server running many jobs at once
 // relies on.  The pool keeps freed memory for later jobs.
+//
+// Failure injection (mc_inject_alloc_failure): with g_fail_after = n >= 0,
+// n more allocations succeed and the next one fails on the host, before any
+// CUDA call, as an out-of-memory would.  g_live counts the allocations held.
+std::atomic<long long> g_fail_after{-1};
+std::atomic<long long> g_live{0};
+
 void raw_free(mc_job* j, void* v) {
-  if (v) cudaFreeAsync(v, j->stream);
+  if (v) {
+    cudaFreeAsync(v, j->stream);
+    g_live.fetch_sub(1);
+  }
 }
 
 cudaError_t raw_alloc(mc_job* j, void** v, size_t bytes) {
-  return cudaMallocAsync(v, bytes ? bytes : 1, j->stream);
+  long long n = g_fail_after.load();
+  while (n >= 0 && !g_fail_after.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n == 0) {
+    *v = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  const cudaError_t e = cudaMallocAsync(v, bytes ? bytes : 1, j->stream);
+  if (e == cudaSuccess) g_live.fetch_add(1);
+  return e;
 }
 
 template <class T>
@@ -104,7 +127,9 @@ void free_all(mc_job* j) {
     raw_free(j, j->d.ckm);
     raw_free(j, j->d.plist);
     raw_free(j, j->d.trace);
+    raw_free(j, j->d.plv);
   }
+  j->d.plv = nullptr;
   j->allocs.clear();
   j->d.plist = nullptr;
   j->d.ckpt = nullptr;
@@ -144,6 +169,13 @@ int sync(mc_job* j, const char* what) {
 extern "C" {
 
 const char* mc_last_error(void) { return g_err.c_str(); }
+
+int mc_inject_alloc_failure(int64_t after) {
+  g_fail_after.store(after < 0 ? -1 : after);
+  return MC_OK;
+}
+
+int64_t mc_live_allocations(void) { return g_live.load(); }
 
 uint64_t mc_kernel_launches(void) { return mcgpu::launches_add(0); }
 
@@ -386,12 +418,29 @@ int round_prepare(mc_job* job, int64_t n_sweeps, uint64_t* t0) {
   return MC_OK;
 }
 
-// A round of n attempts that does not start or end on a sweep: round-start
-// copies for the serial joint's replays; no checkpoints, no trace.
+// A round of n attempts that does not start or end on a sweep: the level of
+// every sample is recorded for the joint when p * n is small enough
+// (kPartialLevelsMax), else round-start copies serve the serial joint's
+// replays; no checkpoints, no trace.
 int attempts_prepare(mc_job* job, int64_t n, uint64_t* t0) {
   if (job->pending) return fail(MC_ESTATE, "previous round not joined");
   if (n < 1 || n >= (int64_t(1) << 34)) return fail(MC_EINVAL, "n_attempts=%lld", static_cast<long long>(n));
   DevJob& d = job->d;
+  const long long entries = static_cast<long long>(job->p) * n;
+  job->attempts_recorded = entries <= job->plv_max;
+  if (job->attempts_recorded && static_cast<size_t>(entries) > job->plv_cap) {
+    if (d.plv) {
+      raw_free(job, d.plv);
+      job->bytes -= job->plv_cap * sizeof(int32_t);
+      d.plv = nullptr;
+      job->plv_cap = 0;
+    }
+    void* v = nullptr;
+    MC_CUDA(raw_alloc(job, &v, static_cast<size_t>(entries) * sizeof(int32_t)), "level record allocation");
+    d.plv = static_cast<int32_t*>(v);
+    job->plv_cap = static_cast<size_t>(entries);
+    job->bytes += job->plv_cap * sizeof(int32_t);
+  }
   const size_t lat = static_cast<size_t>(job->p) * job->L * job->wd;
   MC_CUDA(cudaMemcpyAsync(d.spins0, d.spins, lat * sizeof(uint32_t), cudaMemcpyDeviceToDevice, job->stream),
           "round-start copy");
@@ -418,7 +467,7 @@ int mc_run_attempts(mc_job* job, int64_t n_attempts) {
     return mc_run_sweeps(job, n_attempts / N);
   uint64_t t0 = 0;
   if (int rc = attempts_prepare(job, n_attempts, &t0)) return rc;
-  MC_CUDA(mcgpu::k_generate_attempts(job->d, t0, n_attempts, job->stream), "generation");
+  MC_CUDA(mcgpu::k_generate_attempts(job->d, t0, n_attempts, job->attempts_recorded, job->stream), "generation");
   return MC_OK;
 }
 
@@ -440,7 +489,8 @@ static int join_common(mc_job* job, int64_t* joined_len, bool naive) {
   if (!job->pending) return fail(MC_ESTATE, "no round to join");
   const int64_t M = job->last_M;
   if (job->attempts_round)
-    MC_CUDA(mcgpu::k_join_attempts(job->d, job->t - static_cast<uint64_t>(M), M, job->r, naive, job->stream),
+    MC_CUDA(mcgpu::k_join_attempts(job->d, job->t - static_cast<uint64_t>(M), M, job->r, naive,
+                                   job->attempts_recorded, job->stream),
             "joint");
   else
     MC_CUDA(mcgpu::k_join(job->d, job->shape, job->t - static_cast<uint64_t>(M), job->last_S, job->r, naive,
@@ -822,6 +872,13 @@ int mc_set_join_policy(mc_job* job, int64_t scan_max_samples, int passes_before_
   job->d.scan_max_samples = scan_max_samples < 0 ? mcgpu::kScanMaxSamples : scan_max_samples;
   job->d.passes_scan = passes_before_scan;
   job->d.passes_plain = passes_without_scan;
+  return MC_OK;
+}
+
+int mc_set_partial_record(mc_job* job, int64_t max_entries) {
+  if (int rc = check_job(job)) return rc;
+  if (job->pending) return fail(MC_ESTATE, "round pending");
+  job->plv_max = max_entries < 0 ? mcgpu::kPartialLevelsMax : max_entries;
   return MC_OK;
 }
 

@@ -47,7 +47,7 @@ cudaError_t batch_item(const DevJob& j, const LaunchShape& s, uint64_t t0, int64
   out->trace = trace ? 1 : 0;
   const int per_block = s.cpw * s.wpb;
   const long long per_sweep = static_cast<long long>(per_block) * j.N;
-  const int64_t flushF = std::max<int64_t>(1, 0xFFFFFFFFll / per_sweep);
+  const int64_t flushF = std::max<int64_t>(1, (0xFFFFFFFFll - 32ll * per_block) / per_sweep);
   out->flushF = S > flushF ? flushF : 0;
   *smem_bytes = plan_bytes(j.L, s, true, true);
   *blocks = static_cast<int>(blocks_for(j.p, per_block));

@@ -192,7 +192,8 @@ __device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const u
   Prefetch pf;
   // (one lane a chain: every lane counts; a compile-time 1 keeps the
   // reduction's operand an immediate)
-  GenHook hk{b.hist, GL == 1 ? 1u : (b.owner ? 1u : 0u)};
+  GenHook hk;
+  hk.init(b.hist, GL == 1 ? 1u : (b.owner ? 1u : 0u), j.np1);
   const bool writer = GL == 1 ? b.active : b.owner;
   if (b.active) {
     run.load(j.spins + static_cast<size_t>(b.chain) * j.L * j.wd);
@@ -204,20 +205,29 @@ __device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const u
   // write that only a group's first lane makes, before the next shuffles
   unsigned amask = 0xFFFFFFFFu;
   if constexpr (GL > 1) amask = __ballot_sync(0xFFFFFFFFu, b.active);
+  // countdowns to the next checkpoint and the next histogram flush (no
+  // 64-bit division in the sweep loop)
+  int ck_left = 0, seg = 0;
+  int64_t fl_left = flushF;
   for (int64_t s = 0; s < S; ++s) {
     if (b.active) {
-      if (j.ckpt && (s % j.ck_C) == 0 && writer) {
+      if (j.ckpt && ck_left == 0 && writer) {
         // lattice and level at the start of segment s / C, for the joint's replays
-        const size_t seg = static_cast<size_t>(s / j.ck_C);
-        run.save_strided(j.ckpt + seg * lw * j.p + b.chain, static_cast<size_t>(j.p));
-        j.ckm[seg * j.p + b.chain] = m;
+        run.save_strided(j.ckpt + static_cast<size_t>(seg) * lw * j.p + b.chain, static_cast<size_t>(j.p));
+        j.ckm[static_cast<size_t>(seg) * j.p + b.chain] = m;
       }
       if constexpr (GL > 1) __syncwarp(amask);
       run.template sweep<false, GL>(m, pf, b.T, j.np1, static_cast<uint32_t>(b.chain), j.key0, j.key1, hk);
       if (do_trace && writer) j.trace[s * j.p + b.chain] = 4 * m - 2 * j.N;
       if constexpr (GL > 1) __syncwarp(amask);
     }
-    if (flushF > 0 && (s + 1) % flushF == 0 && s + 1 < S) {
+    if (ck_left == 0) {
+      ck_left = j.ck_C;
+      ++seg;
+    }
+    --ck_left;
+    if (flushF > 0 && --fl_left == 0 && s + 1 < S) {
+      fl_left = flushF;
       if (b.active) hk.flush(m);
       asm volatile("" ::: "memory");
       __syncthreads();
@@ -655,8 +665,9 @@ inline cudaError_t launch_gen_t(const DevJob& j, const LaunchShape& s, uint64_t 
   const int per_block = s.cpw * s.wpb;
   const unsigned grid = blocks_for(j.p, per_block);
   // dwell counts are u32 in shared memory: flush before they can overflow
+  // (up to 32 samples a chain wait one word to be counted)
   const long long per_sweep = static_cast<long long>(per_block) * j.N;
-  const int64_t flushF = std::max<int64_t>(1, 0xFFFFFFFFll / per_sweep);
+  const int64_t flushF = std::max<int64_t>(1, (0xFFFFFFFFll - 32ll * per_block) / per_sweep);
   kern<<<grid, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, S > flushF ? flushF : 0, trace ? 1 : 0);
   launches_add(1);
   return cudaGetLastError();

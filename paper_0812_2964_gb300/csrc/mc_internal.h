@@ -57,7 +57,12 @@ struct DevJob {
   int ck_K;            // segments in the current round
   int kcap;            // segment capacity
   long long* stats;    // [kStatCount] small device counters
+  int32_t* plv;        // [p][M] level after each attempt of a round that is not whole sweeps (nullable)
 };
+
+// rounds that are not whole sweeps record every sample's level (for their
+// parallel joint) when p * M is at most this many entries
+constexpr long long kPartialLevelsMax = 1ll << 26;
 
 // kmin[] value of a chain with no accepted sample found (yet)
 constexpr unsigned long long kNoHit = 0x7FFFFFFFFFFFFFFFull;
@@ -89,10 +94,13 @@ cudaError_t k_order(const DevJob& j, cudaStream_t st);
 cudaError_t k_levels(const DevJob& j, cudaStream_t st);
 cudaError_t k_build_table(const DevJob& j, cudaStream_t st);
 cudaError_t k_update_weights(const DevJob& j, cudaStream_t st);
-// rounds that are not whole sweeps: n attempts per chain from attempt t0,
-// and their joint by the serial rule (M attempts per chain)
-cudaError_t k_generate_attempts(const DevJob& j, uint64_t t0, int64_t n, cudaStream_t st);
-cudaError_t k_join_attempts(const DevJob& j, uint64_t t0, int64_t M, uint32_t r, bool naive, cudaStream_t st);
+// rounds that are not whole sweeps: n attempts per chain from attempt t0
+// (levels recorded in j.plv when `record`), and their joint by the serial
+// rule (M attempts per chain): over the recorded levels, one chain at a time
+// with its samples tested in parallel, else by replay in one thread
+cudaError_t k_generate_attempts(const DevJob& j, uint64_t t0, int64_t n, bool record, cudaStream_t st);
+cudaError_t k_join_attempts(const DevJob& j, uint64_t t0, int64_t M, uint32_t r, bool naive, bool recorded,
+                            cudaStream_t st);
 // E, C, F, S at n inverse temperatures (device arrays betas[n], out[n][4])
 cudaError_t k_thermo(const DevJob& j, const double* betas, int n, double* out, cudaStream_t st);
 cudaError_t k_generate(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S,
@@ -131,6 +139,8 @@ MC_CHAIN_UNIT(chain_kernels_smem_1);
 MC_CHAIN_UNIT(chain_kernels_smem_2);
 MC_CHAIN_UNIT(chain_kernels_smem_3);
 MC_CHAIN_UNIT(chain_kernels_smem_4);
+MC_CHAIN_UNIT(chain_kernels_smem_L16_24);
+MC_CHAIN_UNIT(chain_kernels_smem_L32);
 MC_CHAIN_UNIT(chain_kernels_smem_L48);
 MC_CHAIN_UNIT(chain_kernels_smem_L64);
 MC_CHAIN_UNIT(chain_kernels_smem_L96);

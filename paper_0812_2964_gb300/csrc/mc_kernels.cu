@@ -566,18 +566,90 @@ __device__ __forceinline__ int attempt_one(const DevJob& j, uint32_t* lat, int m
   return m;
 }
 
-__global__ void attempts_kernel(const DevJob j, const uint64_t t0, const int64_t n) {
+__global__ void attempts_kernel(const DevJob j, const uint64_t t0, const int64_t n, int32_t* __restrict__ rec) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= j.p) return;
   uint32_t* lat = j.spins + static_cast<size_t>(c) * j.L * j.wd;
   int m = j.m[c];
   uint4 r = make_uint4(0u, 0u, 0u, 0u);
   uint64_t blk = ~0ull;
+  int32_t* lv = rec ? rec + static_cast<size_t>(c) * n : nullptr;
   for (int64_t k = 0; k < n; ++k) {
     m = attempt_one(j, lat, m, t0 + static_cast<uint64_t>(k), static_cast<uint32_t>(c), r, blk);
     atomicAdd(&j.hgen[m], 1ull);
+    if (lv) lv[k] = m;
   }
   j.m[c] = m;
+}
+
+// The joint of such a round (Sec. 2 steps 3-5) from the recorded levels:
+// the chains in joint order, one at a time (the input of each is the level
+// passed on by those before it), the samples of a chain tested in parallel
+// -- sample k passes iff its joint uniform Philox((k-1)>>2, r, chain, 1)
+// word (k-1)&3 is at most thr(W[m_k] - W[x]) -- in blocks of the block's
+// threads, stopping at the first block with a pass; k_i is the smallest
+// passing k.  The samples before it (all M when none passes) go to dpre.
+__global__ void __launch_bounds__(1024) partial_joint_kernel(const DevJob j, const int64_t M, const uint32_t r) {
+  __shared__ unsigned long long s_k;
+  __shared__ int s_carry, s_valid;
+  const int t = threadIdx.x, nt = blockDim.x;
+  if (t == 0) {
+    s_valid = static_cast<int>(j.stats[kStatCarryValid]);
+    s_carry = static_cast<int>(j.stats[kStatCarry]);
+  }
+  __syncthreads();
+  long long searched = 0;
+  for (int q = 0; q < j.p; ++q) {
+    const int c = j.perm[q];
+    const int valid = s_valid, carry = s_carry;
+    const int32_t* lv = j.plv + static_cast<size_t>(c) * M;
+    __syncthreads();   // everyone has read s_valid / s_carry of this chain
+    if (t == 0) {
+      s_k = kNoHit;
+      j.xused[c] = valid ? carry : -1;
+    }
+    __syncthreads();
+    int64_t kf = 1;   // nothing passed on yet: the chain is kept whole
+    if (valid) {
+      const double wx = j.W[carry];
+      for (int64_t base = 0; base < M; base += nt) {
+        const int64_t k0 = base + t;   // sample k0 + 1
+        bool hit = false;
+        if (k0 < M) {
+          const uint4 v = philox4x32_10(make_uint4(static_cast<uint32_t>(k0 >> 2), r, static_cast<uint32_t>(c), kTagJoint),
+                                        j.key0, j.key1);
+          hit = uint4_word(v, static_cast<uint32_t>(k0 & 3)) <= threshold_det(__dsub_rn(j.W[lv[k0]], wx));
+          ++searched;
+        }
+        if (hit) atomicMin(&s_k, static_cast<unsigned long long>(k0 + 1));
+        if (__syncthreads_or(hit)) break;
+      }
+      kf = s_k == kNoHit ? 0 : static_cast<int64_t>(s_k);
+    }
+    const int64_t nd = kf > 0 ? kf - 1 : M;   // discarded samples
+    for (int64_t k0 = t; k0 < nd; k0 += nt) atomicAdd(&j.dpre[lv[k0]], 1ull);
+    if (t == 0) {
+      j.k[c] = kf;
+      if (kf > 0) {
+        s_carry = j.m[c];
+        s_valid = 1;
+      }
+    }
+    __syncthreads();
+  }
+  if (searched) atomicAdd(reinterpret_cast<unsigned long long*>(&j.stats[kStatSearched]),
+                          static_cast<unsigned long long>(searched));
+  if (t == 0) {
+    j.stats[kStatCarry] = s_carry;
+    j.stats[kStatCarryValid] = s_valid;
+    j.stats[kStatMismatch] = 0;
+    j.stats[kStatPasses] = 0;
+    j.stats[kStatScanned] = 0;
+  }
+}
+
+__global__ void clear_searched_kernel(const DevJob j) {
+  if (threadIdx.x == 0) j.stats[kStatSearched] = 0;
 }
 
 // The joint of such a round by the serial rule itself (Sec. 2 steps 3-5),
@@ -632,16 +704,24 @@ __global__ void serial_joint_kernel(const DevJob j, const uint64_t t0, const int
   j.stats[kStatSearched] = searched;
 }
 
-cudaError_t k_generate_attempts(const DevJob& j, uint64_t t0, int64_t n, cudaStream_t st) {
-  attempts_kernel<<<blocks_for(j.p, 128), 128, 0, st>>>(j, t0, n);
+cudaError_t k_generate_attempts(const DevJob& j, uint64_t t0, int64_t n, bool record, cudaStream_t st) {
+  attempts_kernel<<<blocks_for(j.p, 128), 128, 0, st>>>(j, t0, n, record ? j.plv : nullptr);
   launches_add(1);
   return cudaGetLastError();
 }
 
-cudaError_t k_join_attempts(const DevJob& j, uint64_t t0, int64_t M, uint32_t r, bool naive, cudaStream_t st) {
+cudaError_t k_join_attempts(const DevJob& j, uint64_t t0, int64_t M, uint32_t r, bool naive, bool recorded,
+                            cudaStream_t st) {
   order_kernel<<<1, 1024, 0, st>>>(j);
-  if (naive) naive_kernel<<<blocks_for(j.p, 256), 256, 0, st>>>(j);
-  else serial_joint_kernel<<<1, 32, 0, st>>>(j, t0, M, r);
+  if (naive) {
+    naive_kernel<<<blocks_for(j.p, 256), 256, 0, st>>>(j);
+  } else if (recorded) {
+    clear_searched_kernel<<<1, 32, 0, st>>>(j);
+    partial_joint_kernel<<<1, 1024, 0, st>>>(j, M, r);
+    launches_add(1);
+  } else {
+    serial_joint_kernel<<<1, 32, 0, st>>>(j, t0, M, r);
+  }
   finalize_kernel<<<1, 1024, 0, st>>>(j, M);
   launches_add(3);
   return cudaGetLastError();
@@ -664,7 +744,10 @@ bool shape_supported(int L, const LaunchShape& s) {
 
 LaunchShape default_shape(int L, int p, int num_sms) {
   LaunchShape s;
-  s.placement = (L <= 32) ? kPlaceReg : kPlaceSmem;
+  // lattice rows in registers for L <= 32, except L = 24 and 32, whose
+  // compile-time shared-memory bodies measured faster (L = 32, 16384 chains:
+  // generation 6 % shorter, no rotation of 32 row registers per row)
+  s.placement = (L <= 32 && L != 24 && L != 32) ? kPlaceReg : kPlaceSmem;
   s.wpb = 4;
   const int warps = std::max(1, num_sms) * 4;  // one warp per SM sub-partition
   s.cpw = std::min(32, std::max(1, (p + warps - 1) / warps));
@@ -850,6 +933,9 @@ static cudaError_t dispatch(const DevJob& j, const LaunchShape& s, bool gen, uin
     return chain_kernels_reg_c(j, s, gen, t0, S, trace, r, st);
   }
   switch (j.L) {
+    case 16:
+    case 24: return chain_kernels_smem_L16_24(j, s, gen, t0, S, trace, r, st);
+    case 32: return chain_kernels_smem_L32(j, s, gen, t0, S, trace, r, st);
     case 48: return chain_kernels_smem_L48(j, s, gen, t0, S, trace, r, st);
     case 64: return chain_kernels_smem_L64(j, s, gen, t0, S, trace, r, st);
     case 96: return chain_kernels_smem_L96(j, s, gen, t0, S, trace, r, st);

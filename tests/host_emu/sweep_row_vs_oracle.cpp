@@ -46,7 +46,9 @@ int run(int L, int p, int64_t S, uint64_t seed, const double* W, int start) {
     for (int y = 0; y < L; ++y) for (int x = 0; x < L; ++x) if (s[y * L + x] > 0) lat[y * WD + x / 32] |= 1u << (x % 32);
     int m = m_or;
     std::vector<uint32_t> hist(np1, 0);
-    GenHook hk{hist.data(), 1u};
+    hist.resize(np1 + 3, 0u);          // (scratch counter of the delayed counts past the last level)
+    GenHook hk;
+    hk.init(hist.data(), 1u, np1);
     Prefetch pf; prefetch_init<WD>(pf, L, 0, (uint32_t)c, (uint32_t)seed, (uint32_t)(seed >> 32));
     std::vector<int32_t> tr_g(S);
     for (int64_t sw = 0; sw < S; ++sw) {

@@ -1,6 +1,8 @@
 """Rounds that are not whole sweeps (Sec. 2 step 2 with Fig. 2's M_node =
-100 < N): the GPU's per-attempt path and its serial joint against the
-oracle, bit for bit, alone and mixed with sweep rounds."""
+100 < N): the GPU's per-attempt path and its joint -- over the recorded
+levels with each chain's samples tested in parallel, or by serial replay
+when the record is off -- against the oracle, bit for bit, alone and mixed
+with sweep rounds."""
 import numpy as np
 import pytest
 
@@ -23,11 +25,14 @@ def _same(g, o, L):
     assert np.array_equal(g.energies, 4 * o.levels - 2 * N)
 
 
-@pytest.mark.parametrize("order,naive", [(0, False), (1, False), (0, True)])
-def test_fig2_rounds_match_the_oracle(order, naive):
+@pytest.mark.parametrize("order,naive,record", [(0, False, True), (1, False, True), (0, True, True),
+                                                (0, False, False), (1, False, False)])
+def test_fig2_rounds_match_the_oracle(order, naive, record):
     L, p, n = 20, 32, 100                      # Fig. 2: L = 20, p = 32, M_node = 100
     W = random_weights(L, 20, 4.0)
     g = mc.Job(L, p, 10, 1)
+    if not record:
+        g.set_partial_record(0)                # serial replay joint
     o = oracle.Job(L, p, 10, 1)
     g.weights = W
     o.weights = W
@@ -49,11 +54,14 @@ def test_fig2_rounds_match_the_oracle(order, naive):
         assert np.array_equal(g.weights, o.weights)
 
 
-def test_mixed_round_lengths():
+@pytest.mark.parametrize("record", [True, False])
+def test_mixed_round_lengths(record):
     L, p = 16, 10
     N = L * L
     W = random_weights(L, 3, 6.0)
     g = mc.Job(L, p, 4, 1)
+    if not record:
+        g.set_partial_record(0)
     o = oracle.Job(L, p, 4, 1)
     g.weights = W
     o.weights = W
@@ -82,3 +90,39 @@ def test_batch_refuses_jobs_inside_a_sweep():
     with pytest.raises(mc.McError) as e:
         mc.mc_batch_run([g], 1, 1, 1)
     assert e.value.code == mc.MC_EINVAL
+
+
+def test_long_partial_rounds_with_late_first_passes():
+    # rounds of 3000 attempts (> one block of threads per chain) under rough
+    # weights, so first passing samples fall in later blocks or never
+    L, p, n = 12, 24, 3000
+    W = random_weights(L, 31, 12.0)
+    g = mc.Job(L, p, 13, 1)
+    o = oracle.Job(L, p, 13, 1)
+    g.weights = W
+    o.weights = W
+    g.run_attempts(7)                           # inside a sweep from now on
+    o.run_attempts(7, 4)
+    assert g.join() == o.join()
+    late = 0
+    for _ in range(4):
+        g.run_attempts(n)
+        o.run_attempts(n, 4)
+        _same(g, o, L)
+        assert g.join() == o.join()
+        k = g.k
+        assert np.array_equal(k, o.k)
+        assert np.array_equal(g.hist, o.hist)
+        late += int(((k > 1024) | (k == 0)).sum())
+    assert late > 0
+    assert g.info()["device_bytes"] >= p * n * 4
+
+
+def test_partial_record_argument_checks():
+    g = mc.Job(8, 4, 1, 1)
+    g.run_attempts(10)
+    with pytest.raises(mc.McError) as e:
+        g.set_partial_record(100)
+    assert e.value.code == mc.MC_ESTATE
+    g.join()
+    g.set_partial_record(-1)

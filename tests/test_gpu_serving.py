@@ -39,7 +39,12 @@ def test_results_identical_alone_and_in_the_mix():
         got = [srv.wait(j) for j in ids]
         info = srv.info()
     assert info["completed"] == len(MIX) and info["active"] == 0 and info["queued"] == 0
-    assert 1 <= info["peak_active"] <= 4
+    # continuous batching: several jobs were resident and running at once
+    assert 2 <= info["peak_active"] <= 4
+    spans = [(st["t_admit"], st["t_done"]) for _, st in got]
+    overlapping = [(a, b) for a in range(len(spans)) for b in range(a + 1, len(spans))
+                   if max(spans[a][0], spans[b][0]) < min(spans[a][1], spans[b][1])]
+    assert overlapping, spans
     for (L, p, seed, iters, S), (W, st) in zip(MIX, got):
         W_alone, joined, dev = _alone(L, p, seed, iters, S)
         assert np.array_equal(W, W_alone), f"L={L}"
