@@ -292,6 +292,9 @@ def batch_record(torch, mc, S, steps, warmup, tune, rank=0):
             j.set_trace(True)
             if tune:
                 j.autotune(probe_sweeps=max(1, min(S, 2_000_000 // j.N)))
+        if mode > 0:
+            # shapes of the fused launch from the autotuner (whole-batch probes)
+            mc.mc_batch_autotune(jobs, max(1, min(S, 100)))
         mc.mc_batch_run(jobs, warmup, S, mode)
         torch.cuda.synchronize()
         kept0 = sum(j.info()["total_joined"] for j in jobs)
@@ -302,15 +305,17 @@ def batch_record(torch, mc, S, steps, warmup, tune, rank=0):
         launches = mc.mc_kernel_launches() - l0
         kept = sum(j.info()["total_joined"] for j in jobs) - kept0
         attempts = sum(j.p * S * j.N for j in jobs) * steps
+        shapes = ([list(mc.mc_batch_shape(j)[:3]) for j in jobs] if mode > 0 else
+                  [[j.info()[k] for k in ("placement", "chains_per_warp", "warps_per_block")] for j in jobs])
         out[mode] = {"mode": modes[mode], "value": kept / el, "seconds": el, "kept": kept,
-                     "raw_attempts_per_s": attempts / el, "gpu_launches": launches,
-                     "shapes": [[j.info()[k] for k in ("placement", "chains_per_warp", "warps_per_block")]
-                                for j in jobs]}
+                     "raw_attempts_per_s": attempts / el, "gpu_launches": launches, "shapes": shapes}
         for j in jobs:
             j.close()
     return {"metric": METRIC, "value": out[2]["value"], "unit": UNIT,
             "config": {"workload": "batch_uneven", "groups": [list(g) for g in BATCH_GROUPS],
-                       "sweeps_per_iteration": S, "iterations_timed": steps, "autotuned": bool(tune),
+                       "sweeps_per_iteration": S, "iterations_timed": steps,
+                       "fused_shapes": "mc_batch_autotune (whole-batch probes of min(S, 100) sweeps)",
+                       "per_job_shapes": "mc_autotune" if tune else "library default",
                        "timing": "host wall clock around the synchronising call"},
             "modes": out, "fused_vs_per_job": out[1]["value"] / out[0]["value"],
             "graph_vs_per_job": out[2]["value"] / out[0]["value"], "wall_s": time.perf_counter() - t_wall}

@@ -271,13 +271,35 @@ int mc_set_launch_shape(mc_job *job, int placement, int chains_per_warp, int war
  * update -- Sec. 2 and Eq. new_weight) of n_jobs independent jobs, queued on
  * the first job's stream.  mode 0: one generation launch per job and round;
  * mode 1: one fused generation launch per round for all jobs whose lattice
- * size has a fused form (L = 8, 16, 24, 32 in registers; 48, 64 in shared
- * memory; up to 8 jobs), the others keep their own launch; mode 2: mode 1
- * with the whole loop captured once as a CUDA graph and launched.  The
+ * size has a fused form (L = 8, 16, 24, 32 in registers; 24, 32, 48, 64 in
+ * shared memory; up to 8 jobs), each with the shape mc_batch_autotune chose
+ * for it, or by rule (full warps; shared memory at L = 24, 32, 48, 64), the
+ * others keep their own launch; mode 2: mode 1 with the whole loop captured
+ * once as a CUDA graph and launched.  The
  * chains, and so every result, are the same in all modes.  Synchronises.
  * No round may be pending on any job.  The paper has no counterpart: a
  * scheduling form of running independent weight estimations together. */
 int mc_batch_run(mc_job **jobs, int n_jobs, int iterations, int64_t n_sweeps, int mode);
+
+/* Launch shapes of the jobs in a fused batch launch (mc_batch_run modes 1
+ * and 2), by measurement: each job's candidate shapes (lattice in registers
+ * or shared memory where the fused kernel has that form, 4..32 chains per
+ * warp, lane groups of 4 for shared-memory lattices above L = 32 with at
+ * most 8 chains a warp) are tried in turn, longest chains first, each trial
+ * timed as one whole fused generation launch of all n_jobs jobs of
+ * probe_sweeps sweeps on scratch copies of their chains (CUDA events; the
+ * jobs' own chains do not move); only combinations whose blocks are all
+ * resident on the GPU at once are considered, and a change is kept if it
+ * shortens the launch by more than 1 %.  The result is stored in every job
+ * and used by mc_batch_run; with use_cache != 0 a result found earlier for
+ * the same device and the same (L, n_chains) list is reused without timing.
+ * The chains, and so every result, are the same under any shape.  The paper
+ * has no counterpart (launch tuning).  1 <= n_jobs <= 8; allocates and frees
+ * temporary device memory; synchronises.  mc_batch_shape reports the shape
+ * a job gets in a fused launch and returns 1 if it has a fused form (0 if it
+ * keeps its own launch), or a negative status. */
+int mc_batch_autotune(mc_job **jobs, int n_jobs, int64_t probe_sweeps, int use_cache);
+int mc_batch_shape(mc_job *job, int *placement, int *chains_per_warp, int *warps_per_block);
 
 /* Pick the launch shape by measurement: every supported combination of
  * placement, chains per warp and warps per block is timed on a scratch copy

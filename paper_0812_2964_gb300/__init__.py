@@ -23,7 +23,7 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_get_order", "mc_save", "mc_load", "mc_iteration", "mc_set_join_policy", "mc_run_attempts",
     "mc_set_segment_samples", "mc_set_partial_record", "mc_inject_alloc_failure", "mc_live_allocations",
     "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error",
-    "mc_generate_noalloc", "mc_autotune", "mc_batch_run",
+    "mc_generate_noalloc", "mc_autotune", "mc_batch_run", "mc_batch_autotune", "mc_batch_shape",
     "mc_job_device_bytes", "mc_server_create", "mc_server_submit", "mc_server_poll", "mc_server_wait",
     "mc_server_get_info", "mc_server_clock", "mc_server_free", "Server"]
 
@@ -133,6 +133,9 @@ def lib():
             "mc_sync": (ctypes.c_int, [_vp]),
             "mc_batch_run": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int64, ctypes.c_int]),
+            "mc_batch_autotune": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int64, ctypes.c_int]),
+            "mc_batch_shape": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int)]),
             "mc_autotune": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int)]),
@@ -352,6 +355,26 @@ def mc_batch_run(jobs, iterations: int, n_sweeps: int, mode: int):
     hs = [j.h if isinstance(j, Job) else j for j in jobs]
     arr = (_vp * len(hs))(*[h.value if isinstance(h, _vp) else h for h in hs])
     _check(lib().mc_batch_run(arr, len(hs), iterations, n_sweeps, mode))
+
+
+def _handles(jobs):
+    hs = [j.h if isinstance(j, Job) else j for j in jobs]
+    return (_vp * len(hs))(*[h.value if isinstance(h, _vp) else h for h in hs]), len(hs)
+
+
+def mc_batch_autotune(jobs, probe_sweeps: int, use_cache: bool = True):
+    arr, n = _handles(jobs)
+    _check(lib().mc_batch_autotune(arr, n, probe_sweeps, 1 if use_cache else 0))
+
+
+def mc_batch_shape(job):
+    # (placement, chains per warp, warps per block, has a fused form) of a job in a fused launch
+    pl, c, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rc = lib().mc_batch_shape(job.h if isinstance(job, Job) else job, ctypes.byref(pl), ctypes.byref(c),
+                              ctypes.byref(w))
+    if rc < 0:
+        _check(rc)
+    return int(pl.value), int(c.value), int(w.value), bool(rc)
 
 
 def mc_sync(job):

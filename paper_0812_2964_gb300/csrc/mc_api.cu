@@ -70,6 +70,8 @@ struct mc_job {
   bool trace_valid = false;
   size_t trace_cap = 0;  // int32 elements
   LaunchShape shape;
+  LaunchShape bshape{};          // shape in a fused batch launch (mc_batch_autotune)
+  bool bshape_valid = false;
   int64_t seg_samples = 0;  // target samples per checkpoint segment (0: default)
   size_t bytes = 0;
   std::vector<void*> allocs;
@@ -559,6 +561,19 @@ int mc_update_weights(mc_job* job) {
 }
 
 // ------------------------------------------------------------------ batches
+// Fused-launch shape by rule.  A round takes as long as its slowest chain, so
+// the blocks of all jobs should be resident at once: full warps (few blocks
+// per job), the lattice where a single job runs fastest.  (Lane groups for
+// the shared-memory jobs -- 8 chains a warp, 4 lanes each -- shorten their
+// chains' critical path but need four times the blocks: measured 1.04e11
+// against 1.10e11 kept attempts/s on the uneven batch.)
+static LaunchShape batch_rule_shape(int L, int p) {
+  LaunchShape s{(L <= 32 && L != 24 && L != 32) ? mcgpu::kPlaceReg : mcgpu::kPlaceSmem, std::min(32, p),
+                mcgpu::kBatchWarps};
+  while (s.cpw > 1 && !mcgpu::batch_supported(L, s)) s.cpw >>= 1;
+  return s;
+}
+
 // `iterations` weight iterations of several independent jobs, everything on
 // the first job's stream: per iteration every job runs one round of n_sweeps
 // sweeps, is joined and updates its weight.  mode 0: one generation launch
@@ -586,19 +601,12 @@ static int mc_batch_run_impl(mc_job** jobs, int n_jobs, int iterations, int64_t 
     saved[i] = jobs[i]->stream;
     jobs[i]->stream = st;
   }
-  // shapes for the fused launch.  A round takes as long as its slowest chain,
-  // so the blocks of all jobs should be resident at once: few warps per job,
-  // the longest chains first (below).
+  // shapes for the fused launch: the autotuned ones (mc_batch_autotune), else
+  // the rule of batch_rule_shape
   std::vector<LaunchShape> bshape(n_jobs);
   std::vector<char> fused(n_jobs, 0);
   for (int i = 0; i < n_jobs && mode > 0; ++i) {
-    // full warps.  (Lane groups for the shared-memory jobs -- 8 chains a
-    // warp, 4 lanes each -- shorten their chains' critical path but need
-    // four times the blocks, which then no longer all fit at once: measured
-    // 1.04e11 against 1.10e11 kept attempts/s on the uneven batch.)
-    LaunchShape s{jobs[i]->L <= 32 ? mcgpu::kPlaceReg : mcgpu::kPlaceSmem, std::min(32, jobs[i]->p),
-                  mcgpu::kBatchWarps};
-    while (s.cpw > 1 && !mcgpu::batch_supported(jobs[i]->L, s)) s.cpw >>= 1;
+    const LaunchShape s = jobs[i]->bshape_valid ? jobs[i]->bshape : batch_rule_shape(jobs[i]->L, jobs[i]->p);
     bshape[i] = s;
     fused[i] = mcgpu::batch_supported(jobs[i]->L, s) ? 1 : 0;
   }
@@ -1142,6 +1150,173 @@ int mc_autotune(mc_job* job, int64_t probe_sweeps, int use_cache, int* placement
   } catch (...) {
     return fail(MC_EINVAL, "mc_autotune: unexpected host error");
   }
+}
+
+// Fused-batch autotuner: greedy over each job's candidate shapes (placement,
+// chains per warp; lane groups follow from them), every candidate timed as a
+// whole fused generation launch of all jobs on scratch copies of their
+// chains (CUDA events; the jobs' own chains do not move), keeping only
+// combinations whose blocks are all resident at once.  Jobs are visited from
+// the longest chains (largest N) down; a candidate is kept if it shortens the
+// launch by more than 1 %.  Cached per (device, the jobs' (L, p) in order).
+namespace {
+std::map<std::vector<int>, std::vector<LaunchShape>> g_btune_cache;
+}  // namespace
+
+static int mc_batch_autotune_impl(mc_job** jobs, int n_jobs, int64_t probe_sweeps, int use_cache) {
+  if (!jobs || n_jobs < 1 || n_jobs > mcgpu::kMaxBatch) return fail(MC_EINVAL, "need 1..%d jobs", mcgpu::kMaxBatch);
+  if (probe_sweeps < 1) return fail(MC_EINVAL, "bad probe_sweeps");
+  for (int i = 0; i < n_jobs; ++i) {
+    if (!jobs[i]) return fail(MC_EINVAL, "job %d is null", i);
+    if (jobs[i]->pending) return fail(MC_ESTATE, "job %d has a round pending", i);
+    if (jobs[i]->device != jobs[0]->device) return fail(MC_EINVAL, "jobs on different devices");
+    if (probe_sweeps * jobs[i]->N >= (int64_t(1) << 34)) return fail(MC_EINVAL, "bad probe_sweeps");
+    for (int k = 0; k < i; ++k)
+      if (jobs[k] == jobs[i]) return fail(MC_EINVAL, "job %d listed twice", i);
+  }
+  std::vector<int> key{jobs[0]->device};
+  for (int i = 0; i < n_jobs; ++i) {
+    key.push_back(jobs[i]->L);
+    key.push_back(jobs[i]->p);
+  }
+  if (use_cache) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_btune_cache.find(key);
+    if (it != g_btune_cache.end()) {
+      for (int i = 0; i < n_jobs; ++i) {
+        jobs[i]->bshape = it->second[i];
+        jobs[i]->bshape_valid = true;
+      }
+      return MC_OK;
+    }
+  }
+  // candidates per job (the rule first); jobs without a fused form keep it
+  std::vector<std::vector<LaunchShape>> cands(n_jobs);
+  std::vector<LaunchShape> cur(n_jobs);
+  for (int i = 0; i < n_jobs; ++i) {
+    cur[i] = batch_rule_shape(jobs[i]->L, jobs[i]->p);
+    cands[i].push_back(cur[i]);
+    if (!mcgpu::batch_supported(jobs[i]->L, cur[i])) continue;
+    for (int pl = 0; pl < 2; ++pl)
+      for (int c : {32, 16, 8, 4}) {
+        const LaunchShape s{pl, std::min(c, jobs[i]->p), mcgpu::kBatchWarps};
+        if (!mcgpu::batch_supported(jobs[i]->L, s)) continue;
+        bool dup = false;
+        for (const auto& q : cands[i]) dup = dup || (q.placement == s.placement && q.cpw == s.cpw);
+        if (!dup) cands[i].push_back(s);
+      }
+  }
+  std::vector<int> order(n_jobs);
+  for (int i = 0; i < n_jobs; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a]->N > jobs[b]->N; });
+  // scratch copies of every job's chains
+  cudaStream_t st = jobs[0]->stream;
+  std::vector<DevJob> d(n_jobs);
+  std::vector<void*> mem;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < n_jobs && e == cudaSuccess; ++i) {
+    e = cudaStreamSynchronize(jobs[i]->stream);
+    d[i] = jobs[i]->d;
+    const size_t lat = static_cast<size_t>(jobs[i]->p) * jobs[i]->L * jobs[i]->wd;
+    void *sp = nullptr, *sm = nullptr, *sh = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&sp, lat * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&sm, static_cast<size_t>(jobs[i]->p) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&sh, static_cast<size_t>(d[i].np1) * 8);
+    for (void* v : {sp, sm, sh})
+      if (v) mem.push_back(v);
+    d[i].spins = static_cast<uint32_t*>(sp);
+    d[i].m = static_cast<int32_t*>(sm);
+    d[i].hgen = static_cast<unsigned long long*>(sh);
+    d[i].trace = nullptr;
+    d[i].ckpt = nullptr;   // probes write no checkpoints
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  // time of one fused launch with these shapes (1e30 if its blocks would not all be resident)
+  auto probe = [&](const std::vector<LaunchShape>& sh) -> float {
+    mcgpu::BatchParams P;
+    P.n = 0;
+    size_t smem = 0;
+    int blocks = 0;
+    for (int oi = 0; oi < n_jobs; ++oi) {
+      const int i = order[oi];
+      if (!mcgpu::batch_supported(jobs[i]->L, sh[i])) continue;
+      mcgpu::BatchItem& item = P.items[P.n++];
+      size_t b = 0;
+      int nb = 0;
+      mcgpu::batch_item(d[i], sh[i], jobs[i]->t, probe_sweeps, false, &item, &b, &nb);
+      item.first_block = blocks;
+      blocks += nb;
+      smem = std::max(smem, b);
+    }
+    if (P.n == 0 || blocks > mcgpu::batch_resident_blocks(smem)) return 1e30f;
+    float ms = 1e30f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first run warms up
+      for (int i = 0; i < n_jobs && e == cudaSuccess; ++i) {
+        const size_t lat = static_cast<size_t>(jobs[i]->p) * jobs[i]->L * jobs[i]->wd;
+        e = cudaMemcpyAsync(d[i].spins, jobs[i]->d.spins, lat * 4, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(d[i].m, jobs[i]->d.m, static_cast<size_t>(jobs[i]->p) * 4, cudaMemcpyDeviceToDevice, st);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) e = mcgpu::k_generate_batched(P, smem, blocks, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    return e == cudaSuccess ? ms : 1e30f;
+  };
+  if (e == cudaSuccess) {
+    float best = probe(cur);
+    for (int oi = 0; oi < n_jobs && e == cudaSuccess; ++oi) {
+      const int i = order[oi];
+      for (const auto& c : cands[i]) {
+        if (c.placement == cur[i].placement && c.cpw == cur[i].cpw) continue;
+        std::vector<LaunchShape> trial = cur;
+        trial[i] = c;
+        const float t = probe(trial);
+        if (e != cudaSuccess) break;
+        if (t < 0.99f * best) {
+          best = t;
+          cur = trial;
+        }
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  for (void* v : mem) cudaFree(v);
+  if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
+  for (int i = 0; i < n_jobs; ++i) {
+    jobs[i]->bshape = cur[i];
+    jobs[i]->bshape_valid = true;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_btune_cache[key] = cur;
+  }
+  return MC_OK;
+}
+
+// (host allocations inside may throw; nothing crosses the ABI)
+int mc_batch_autotune(mc_job** jobs, int n_jobs, int64_t probe_sweeps, int use_cache) {
+  try {
+    return mc_batch_autotune_impl(jobs, n_jobs, probe_sweeps, use_cache);
+  } catch (const std::bad_alloc&) {
+    return fail(MC_ENOMEM, "mc_batch_autotune: host allocation failed");
+  } catch (...) {
+    return fail(MC_EINVAL, "mc_batch_autotune: unexpected host error");
+  }
+}
+
+int mc_batch_shape(mc_job* job, int* placement, int* chains_per_warp, int* warps_per_block) {
+  if (int rc = check_job(job)) return rc;
+  const LaunchShape s = job->bshape_valid ? job->bshape : batch_rule_shape(job->L, job->p);
+  if (placement) *placement = s.placement;
+  if (chains_per_warp) *chains_per_warp = s.cpw;
+  if (warps_per_block) *warps_per_block = s.wpb;
+  return mcgpu::batch_supported(job->L, s) ? 1 : 0;
 }
 
 uint64_t mc_job_device_bytes(int L, int n_chains, int64_t sweeps) {

@@ -258,34 +258,37 @@ __device__ __forceinline__ void sweep_row(uint32_t (&cur)[WD], const uint32_t (&
 // compile-time constant once the site loop is unrolled.
 //
 // Generation: every sample adds 1 to its level's u32 counter in the block's
-// shared-memory histogram (one reduction, no branch), one lattice word late:
-// the sample at site b of a word is counted while site b of the next word is
-// attempted, its level waiting in pend[b] meanwhile.  A reduction issued
-// right after the level update sat on the chain's serial path -- the next
-// site's threshold loads are shared-memory accesses of the same warp and
-// stay behind it -- while one whose address is known a word early does not
-// (measured at L = 32: 9 % off the generation time).  pend[] starts at a
-// scratch counter past the last level; flush() counts what is pending.
+// shared-memory histogram (one reduction, no branch), D sites late: the
+// sample at site b is counted while site b + D is attempted (D divides 32,
+// so the slot b % D is a compile-time register), its level waiting in
+// pend[b % D] meanwhile.  A reduction issued right after the level update
+// sat on the chain's serial path -- the next site's threshold loads are
+// shared-memory accesses of the same warp and stay behind it -- while one
+// whose address is known sites early does not (measured at L = 32 with
+// D = 32: 9 % off the generation time).  pend[] starts at a scratch counter
+// past the last level; flush() counts what is pending.  D = 32 for one word
+// a row; 8 where the row's words already fill the registers.
+template <int D = 32>
 struct GenHook {
   uint32_t* hist;
   uint32_t inc;      // 1; 0 for the lanes of a lane group that only help (one count per chain)
   int scratch;       // byte offset of the scratch counter (4 (N+1))
-  int pend[32];      // byte offsets (4 m) of the samples not counted yet
+  int pend[D];       // byte offsets (4 m) of the samples not counted yet
   __device__ __forceinline__ void init(uint32_t* h, uint32_t i, int np1) {
     hist = h;
     inc = i;
     scratch = 4 * np1;
 #pragma unroll
-    for (int b = 0; b < 32; ++b) pend[b] = scratch;
+    for (int b = 0; b < D; ++b) pend[b] = scratch;
   }
   __device__ __forceinline__ void word(int) {}
   __device__ __forceinline__ void sample(int m4, int b) {
-    red_shared_add(hist, pend[b], inc);
-    pend[b] = m4;
+    red_shared_add(hist, pend[b % D], inc);
+    pend[b % D] = m4;
   }
   __device__ __forceinline__ void flush(int) {
 #pragma unroll
-    for (int b = 0; b < 32; ++b) {
+    for (int b = 0; b < D; ++b) {
       red_shared_add(hist, pend[b], inc);
       pend[b] = scratch;
     }

@@ -192,7 +192,7 @@ __device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const u
   Prefetch pf;
   // (one lane a chain: every lane counts; a compile-time 1 keeps the
   // reduction's operand an immediate)
-  GenHook hk;
+  GenHook<decltype(run)::WD == 1 ? 32 : 8> hk;
   hk.init(b.hist, GL == 1 ? 1u : (b.owner ? 1u : 0u), j.np1);
   const bool writer = GL == 1 ? b.active : b.owner;
   if (b.active) {

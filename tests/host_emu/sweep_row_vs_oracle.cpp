@@ -47,7 +47,7 @@ int run(int L, int p, int64_t S, uint64_t seed, const double* W, int start) {
     int m = m_or;
     std::vector<uint32_t> hist(np1, 0);
     hist.resize(np1 + 3, 0u);          // (scratch counter of the delayed counts past the last level)
-    GenHook hk;
+    GenHook<WD == 1 ? 32 : 8> hk;
     hk.init(hist.data(), 1u, np1);
     Prefetch pf; prefetch_init<WD>(pf, L, 0, (uint32_t)c, (uint32_t)seed, (uint32_t)(seed >> 32));
     std::vector<int32_t> tr_g(S);

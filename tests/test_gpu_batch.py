@@ -52,6 +52,35 @@ def test_batch_modes_match_single_jobs(reference, mode):
         assert j.info()["rounds_joined"] == 3
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_autotuned_batch_matches_single_jobs(reference, mode):
+    # shapes picked by timing whole fused launches; the chains are the same
+    js = _jobs(trace=False)
+    mc.mc_batch_autotune(js, 2, use_cache=False)
+    shapes = [mc.mc_batch_shape(j) for j in js]
+    assert all(w == 4 for (_, _, w, _) in shapes)
+    assert [f for (*_, f) in shapes] == [True, True, True, True, False]   # L = 12 keeps its own launch
+    mc.mc_batch_autotune(js, 2, use_cache=True)                          # cached: same shapes
+    assert [mc.mc_batch_shape(j) for j in js] == shapes
+    mc.mc_batch_run(js, 3, 3, mode)
+    for j, ref in zip(js, reference):
+        got = _state(j)
+        for a, b in zip(got[:4], ref[:4]):
+            assert np.array_equal(a, b)
+        assert got[4] == ref[4]
+
+
+def test_batch_autotune_argument_checks():
+    js = _jobs(trace=False)
+    with pytest.raises(mc.McError) as e:
+        mc.mc_batch_autotune(js, 0)
+    assert e.value.code == mc.MC_EINVAL
+    js[0].run_sweeps(1)
+    with pytest.raises(mc.McError) as e:
+        mc.mc_batch_autotune(js, 1)
+    assert e.value.code == mc.MC_ESTATE
+
+
 def test_batch_rejects_pending_and_duplicates():
     js = _jobs(trace=False)
     with pytest.raises(mc.McError):
