@@ -627,7 +627,8 @@ def run_fig2(args):
         out[name] = {"E_per_site": [float(e) for e in E], "deviation": dev,
                      "max_abs_dev_beta_le_0.44": max(abs(d) for b, d in zip(betas, dev) if b <= 0.45),
                      "max_abs_dev_beta_gt_0.44": max(abs(d) for b, d in zip(betas, dev) if b > 0.45),
-                     "rounds": rounds, "seconds": el}
+                     "rounds": rounds, "seconds": el, "ms_per_round": 1e3 * el / max(1, rounds),
+                     "kept_fraction": iters * M_total / max(1, rounds * p * M_node)}
         job.close()
     line = {"metric": "fig2: E/N deviation from the exact L=20 values", "unit": "energy per site",
             "value": out["detailed balance"]["max_abs_dev_beta_le_0.44"], "higher_is_better": False,
@@ -662,7 +663,7 @@ def main(argv=None):
     ap.add_argument("--slots", type=int, default=64, help="serving: server slots")
     ap.add_argument("--join-order", type=int, default=0,
                     help="0: chains joined in index order; 1: by ascending final energy (end of Sec. 2)")
-    ap.add_argument("--mtotal", type=int, default=1_000_000, help="fig2: samples per weight iteration")
+    ap.add_argument("--mtotal", type=int, default=100_000_000, help="fig2: samples per weight iteration (M_total)")
     ap.add_argument("--iters", type=int, default=20, help="fig2: weight iterations")
     ap.add_argument("--mnode", type=int, default=100, help="fig2: attempts per chain per round (M_node)")
     args = ap.parse_args(argv)

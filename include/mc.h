@@ -113,6 +113,16 @@ int mc_run_sweeps(mc_job *job, int64_t n_sweeps);
  * Asynchronous; MC_ESTATE if the previous round has not been joined. */
 int mc_run_attempts(mc_job *job, int64_t n_attempts);
 
+/* Largest whole-sweep round (p * M samples) whose levels generation records,
+ * 2 bytes a sample, for the joint to read instead of replaying the chains
+ * from checkpoints (performance and memory only: both give the serial
+ * rule's result).  The default is 2^29 for L > 64, where the threshold
+ * table does not fit in shared memory and replays are slow, and 0 (no
+ * record) for L <= 64; max_samples < 0 restores it, 0 turns the record off.
+ * Rounds of mc_batch_run are not recorded.  MC_ESTATE while a round is
+ * pending. */
+int mc_set_round_record(mc_job *job, int64_t max_samples);
+
 /* Largest record (p * n_attempts entries, int32 each) that a round of
  * mc_run_attempts keeps for its joint; larger rounds are joined by serial
  * replay (performance and memory only: both give the serial rule's result).

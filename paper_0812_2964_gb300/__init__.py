@@ -21,7 +21,7 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_get_table", "mc_get_spins", "mc_set_spins", "mc_get_energies", "mc_get_trace",
     "mc_get_trace_chain", "mc_get_visited", "mc_set_visited", "mc_thermo", "mc_set_join_order",
     "mc_get_order", "mc_save", "mc_load", "mc_iteration", "mc_set_join_policy", "mc_run_attempts",
-    "mc_set_segment_samples", "mc_set_partial_record", "mc_inject_alloc_failure", "mc_live_allocations",
+    "mc_set_segment_samples", "mc_set_partial_record", "mc_set_round_record", "mc_inject_alloc_failure", "mc_live_allocations",
     "mc_get_join", "mc_get_info", "mc_set_launch_shape", "mc_sync", "mc_last_error",
     "mc_generate_noalloc", "mc_autotune", "mc_batch_run", "mc_batch_autotune", "mc_batch_shape",
     "mc_job_device_bytes", "mc_server_create", "mc_server_submit", "mc_server_poll", "mc_server_wait",
@@ -122,6 +122,7 @@ def lib():
             "mc_set_join_policy": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int]),
             "mc_set_segment_samples": (ctypes.c_int, [_vp, ctypes.c_int64]),
             "mc_set_partial_record": (ctypes.c_int, [_vp, ctypes.c_int64]),
+            "mc_set_round_record": (ctypes.c_int, [_vp, ctypes.c_int64]),
             "mc_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
             "mc_iteration": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                             _i64p, ctypes.POINTER(ctypes.c_int)]),
@@ -301,6 +302,10 @@ def mc_load(path: str):
 def mc_set_join_policy(job, scan_max_samples: int = -1, passes_before_scan: int = 2,
                        passes_without_scan: int = 10):
     _check(lib().mc_set_join_policy(job, scan_max_samples, passes_before_scan, passes_without_scan))
+
+
+def mc_set_round_record(job, max_samples: int):
+    _check(lib().mc_set_round_record(job, int(max_samples)))
 
 
 def mc_set_partial_record(job, max_entries: int):
@@ -526,6 +531,9 @@ class Job:
 
     def set_partial_record(self, max_entries: int):
         mc_set_partial_record(self.h, max_entries)
+
+    def set_round_record(self, max_samples: int):
+        mc_set_round_record(self.h, max_samples)
 
     @property
     def order(self):

@@ -65,6 +65,9 @@ struct mc_job {
   bool attempts_recorded = false;  // ... and its samples' levels are in d.plv
   size_t plv_cap = 0;           // int32 entries of d.plv
   long long plv_max = mcgpu::kPartialLevelsMax;  // largest p * M recorded
+  uint16_t* rec_buf = nullptr;  // record of whole-sweep rounds (d.rec points here when used)
+  size_t rec_cap = 0;           // uint16 entries of rec_buf
+  long long rec_max = 0;                         // largest p * M recorded (set by mc_init)
   bool pending = false;
   bool trace_on = false;
   bool trace_valid = false;
@@ -130,8 +133,11 @@ void free_all(mc_job* j) {
     raw_free(j, j->d.plist);
     raw_free(j, j->d.trace);
     raw_free(j, j->d.plv);
+    raw_free(j, j->rec_buf);
   }
   j->d.plv = nullptr;
+  j->rec_buf = nullptr;
+  j->d.rec = nullptr;
   j->allocs.clear();
   j->d.plist = nullptr;
   j->d.ckpt = nullptr;
@@ -256,6 +262,7 @@ static int mc_init_impl(int L, int n_chains, uint64_t seed, int start, mc_job** 
     return rc;
   }
   j->shape = mcgpu::default_shape(L, n_chains, j->num_sms);
+  j->rec_max = mcgpu::default_record_max(L);
   *out = j;
   return MC_OK;
 }
@@ -389,9 +396,34 @@ int ensure_trace(mc_job* job, int64_t n_sweeps) {
   return MC_OK;
 }
 
+// Record buffer for a whole-sweep round of p * M samples (uint16 each), or
+// none when the round is larger than the job's limit (the joint replays).
+int ensure_record(mc_job* job, long long samples, bool allow) {
+  DevJob& d = job->d;
+  d.rec = nullptr;
+  if (!allow || samples > job->rec_max) return MC_OK;
+  if (static_cast<size_t>(samples) > job->rec_cap) {
+    if (job->rec_buf) {
+      raw_free(job, job->rec_buf);
+      job->bytes -= job->rec_cap * sizeof(uint16_t);
+      job->rec_buf = nullptr;
+      job->rec_cap = 0;
+    }
+    void* v = nullptr;
+    MC_CUDA(raw_alloc(job, &v, static_cast<size_t>(samples) * sizeof(uint16_t)), "round record allocation");
+    job->rec_buf = static_cast<uint16_t*>(v);
+    job->rec_cap = static_cast<size_t>(samples);
+    job->bytes += job->rec_cap * sizeof(uint16_t);
+  }
+  d.rec = job->rec_buf;
+  return MC_OK;
+}
+
 // Start a round: checks, round-start copies (for the joint's replays) and the
-// host bookkeeping; *t0 = attempts each chain made before this round.
-int round_prepare(mc_job* job, int64_t n_sweeps, uint64_t* t0) {
+// host bookkeeping; *t0 = attempts each chain made before this round.  With
+// allow_record the round's levels are recorded when it is small enough (the
+// fused batch launch writes no record).
+int round_prepare(mc_job* job, int64_t n_sweeps, uint64_t* t0, bool allow_record = true) {
   if (job->pending) return fail(MC_ESTATE, "previous round not joined");
   if (n_sweeps < 1) return fail(MC_EINVAL, "n_sweeps=%lld", static_cast<long long>(n_sweeps));
   const int64_t M = n_sweeps * job->N;
@@ -402,6 +434,7 @@ int round_prepare(mc_job* job, int64_t n_sweeps, uint64_t* t0) {
   int K = 0, C = 0;
   round_segments(job->L, job->p, n_sweeps, job->seg_samples, &K, &C);
   if (int rc = ensure_segments(job, K)) return rc;
+  if (int rc = ensure_record(job, static_cast<long long>(job->p) * M, allow_record)) return rc;
   DevJob& d = job->d;
   d.ck_K = K;
   d.ck_C = C;
@@ -428,6 +461,7 @@ int attempts_prepare(mc_job* job, int64_t n, uint64_t* t0) {
   if (job->pending) return fail(MC_ESTATE, "previous round not joined");
   if (n < 1 || n >= (int64_t(1) << 34)) return fail(MC_EINVAL, "n_attempts=%lld", static_cast<long long>(n));
   DevJob& d = job->d;
+  d.rec = nullptr;   // (their levels go to plv)
   const long long entries = static_cast<long long>(job->p) * n;
   job->attempts_recorded = entries <= job->plv_max;
   if (job->attempts_recorded && static_cast<size_t>(entries) > job->plv_cap) {
@@ -636,7 +670,7 @@ static int mc_batch_run_impl(mc_job** jobs, int n_jobs, int iterations, int64_t 
     for (int oi = 0; oi < n_jobs && rc == MC_OK; ++oi) {
       const int i = order[oi];
       uint64_t t0 = 0;
-      if ((rc = round_prepare(jobs[i], n_sweeps, &t0))) break;
+      if ((rc = round_prepare(jobs[i], n_sweeps, &t0, false))) break;
       cudaError_t e = cudaSuccess;
       if (mode > 0 && fused[i]) {
         mcgpu::BatchItem& item = P.items[P.n++];
@@ -883,6 +917,13 @@ int mc_set_join_policy(mc_job* job, int64_t scan_max_samples, int passes_before_
   return MC_OK;
 }
 
+int mc_set_round_record(mc_job* job, int64_t max_samples) {
+  if (int rc = check_job(job)) return rc;
+  if (job->pending) return fail(MC_ESTATE, "round pending");
+  job->rec_max = max_samples < 0 ? mcgpu::default_record_max(job->L) : max_samples;
+  return MC_OK;
+}
+
 int mc_set_partial_record(mc_job* job, int64_t max_entries) {
   if (int rc = check_job(job)) return rc;
   if (job->pending) return fail(MC_ESTATE, "round pending");
@@ -1105,6 +1146,7 @@ static int mc_autotune_impl(mc_job* job, int64_t probe_sweeps, int use_cache, in
     d.hgen = static_cast<unsigned long long*>(sh);
     d.trace = nullptr;
     d.ckpt = nullptr;  // probes write no checkpoints
+    d.rec = nullptr;   // nor records
     for (const auto& s : cands) {
       float ms = 0.f;
       for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms up
@@ -1229,6 +1271,7 @@ static int mc_batch_autotune_impl(mc_job** jobs, int n_jobs, int64_t probe_sweep
     d[i].hgen = static_cast<unsigned long long*>(sh);
     d[i].trace = nullptr;
     d[i].ckpt = nullptr;   // probes write no checkpoints
+    d[i].rec = nullptr;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
@@ -1330,7 +1373,9 @@ uint64_t mc_job_device_bytes(int L, int n_chains, int64_t sweeps) {
   int K = 0, C = 0;
   round_segments(L, n_chains, sweeps, 0, &K, &C);
   (void)lw;
-  return b + static_cast<uint64_t>(K) * bytes_per_segment(L, n_chains);
+  const uint64_t samples = p * static_cast<uint64_t>(sweeps) * N;   // record of the round, if small
+  const uint64_t rec = samples <= static_cast<uint64_t>(mcgpu::default_record_max(L)) ? samples * 2 : 0;
+  return b + static_cast<uint64_t>(K) * bytes_per_segment(L, n_chains) + rec;
 }
 
 int mc_sync(mc_job* job) {

@@ -268,16 +268,28 @@ __device__ __forceinline__ void sweep_row(uint32_t (&cur)[WD], const uint32_t (&
 // D = 32: 9 % off the generation time).  pend[] starts at a scratch counter
 // past the last level; flush() counts what is pending.  D = 32 for one word
 // a row; 8 where the row's words already fill the registers.
-template <int D = 32>
+//
+// REC: the round is recorded -- every sample's level is also stored, as a
+// uint16, in the chain's row of the record (its samples in order), four
+// samples to one 8-byte store (rows and lattice words hold multiples of
+// four sites, so site b of a word is sample b mod 4 of its group), for the
+// joint to read instead of replaying.
+template <int D = 32, bool REC = false>
 struct GenHook {
   uint32_t* hist;
   uint32_t inc;      // 1; 0 for the lanes of a lane group that only help (one count per chain)
   int scratch;       // byte offset of the scratch counter (4 (N+1))
   int pend[D];       // byte offsets (4 m) of the samples not counted yet
+  uint16_t* rec;     // REC: the chain's next record entry (always a valid address)
+  bool rec_on;       // REC: this lane writes the record (one lane per chain)
+  uint32_t pk0, pk1; // REC: levels of the current group of four samples
   __device__ __forceinline__ void init(uint32_t* h, uint32_t i, int np1) {
     hist = h;
     inc = i;
     scratch = 4 * np1;
+    rec = nullptr;
+    rec_on = false;
+    pk0 = pk1 = 0u;
 #pragma unroll
     for (int b = 0; b < D; ++b) pend[b] = scratch;
   }
@@ -285,6 +297,18 @@ struct GenHook {
   __device__ __forceinline__ void sample(int m4, int b) {
     red_shared_add(hist, pend[b % D], inc);
     pend[b % D] = m4;
+    if constexpr (REC) {
+      const uint32_t lv = static_cast<uint32_t>(m4) >> 2;
+      switch (b & 3) {
+        case 0: pk0 = lv; break;
+        case 1: pk0 |= lv << 16; break;
+        case 2: pk1 = lv; break;
+        default:
+          pk1 |= lv << 16;
+          if (rec_on) *reinterpret_cast<uint2*>(rec) = make_uint2(pk0, pk1);
+          rec += 4;
+      }
+    }
   }
   __device__ __forceinline__ void flush(int) {
 #pragma unroll

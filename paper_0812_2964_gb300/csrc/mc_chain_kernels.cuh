@@ -180,7 +180,7 @@ struct RunnerFactorySmem {
 // lane group share one chain -- same lattice column, same uniforms (split
 // between them, see philox_fill) -- and only the group's first lane writes
 // counts, checkpoints, trace and the final state.
-template <class Factory, bool TSMEM, int GL = 1>
+template <class Factory, bool TSMEM, int GL = 1, bool REC = false>
 __device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const uint64_t t0, const int64_t S,
                                          const int64_t flushF, const int do_trace, const int block) {
   const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, true);
@@ -192,9 +192,16 @@ __device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const u
   Prefetch pf;
   // (one lane a chain: every lane counts; a compile-time 1 keeps the
   // reduction's operand an immediate)
-  GenHook<decltype(run)::WD == 1 ? 32 : 8> hk;
+  GenHook<decltype(run)::WD == 1 ? 32 : 8, REC> hk;
   hk.init(b.hist, GL == 1 ? 1u : (b.owner ? 1u : 0u), j.np1);
   const bool writer = GL == 1 ? b.active : b.owner;
+  if constexpr (REC) {
+    // the chain's row of the record; every lane of a group keeps a valid
+    // address (pointer arithmetic on a null pointer would let the compiler
+    // drop the writer test), only the writer stores
+    hk.rec = j.rec + static_cast<size_t>(b.active ? b.chain : 0) * static_cast<size_t>(S * j.N);
+    hk.rec_on = writer;
+  }
   if (b.active) {
     run.load(j.spins + static_cast<size_t>(b.chain) * j.L * j.wd);
     m = j.m[b.chain];
@@ -254,10 +261,10 @@ __device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const u
   }
 }
 
-template <class Factory, bool TSMEM, int GL = 1>
+template <class Factory, bool TSMEM, int GL = 1, bool REC = false>
 __global__ void __launch_bounds__(128) gen_kernel(const DevJob j, const int cpw, const uint64_t t0,
                                                   const int64_t S, const int64_t flushF, const int do_trace) {
-  gen_body<Factory, TSMEM, GL>(j, cpw, t0, S, flushF, do_trace, blockIdx.x);
+  gen_body<Factory, TSMEM, GL, REC>(j, cpw, t0, S, flushF, do_trace, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ joint: replays
@@ -293,6 +300,39 @@ __device__ __forceinline__ void replay_segment(const DevJob& j, const BlockCtx& 
   for (int64_t s = s0; s < s1 && !hk.done; ++s) {
     run.template sweep<true>(m, pf, b.T, j.np1, static_cast<uint32_t>(i), j.key0, j.key1, hk);
     hk.poll();
+  }
+}
+
+// The same samples as replay_segment, read from the round's record of
+// levels (generation stored them, one row of M uint16 a chain): a hook sees
+// word(nb) before every 32 samples and sample(4 m, b) for each, in order; no
+// Metropolis replay.  The joint uniforms of a hook depend only on the
+// sample's index, so words need not follow lattice rows.  A lane reads its
+// chain's row 16 bytes at a time (segments start on multiples of 16
+// samples, and hold multiples of 16).
+template <class Hook>
+__device__ __forceinline__ void record_segment(const DevJob& j, int i, int seg, int64_t S, Hook& hk) {
+  const int64_t k0 = static_cast<int64_t>(seg) * j.ck_C * j.N;
+  const int64_t k1 = min(S, static_cast<int64_t>(seg + 1) * j.ck_C) * j.N;
+  const uint16_t* row = j.rec + static_cast<size_t>(i) * static_cast<size_t>(S * j.N);
+  int words = 0;
+  for (int64_t kb = k0; kb < k1 && !hk.done; kb += 32) {
+    const int nb = static_cast<int>(min(static_cast<int64_t>(32), k1 - kb));
+    const uint4* src = reinterpret_cast<const uint4*>(row + kb);
+    uint4 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = (8 * q < nb) ? __ldg(src + q) : make_uint4(0u, 0u, 0u, 0u);
+    hk.word(nb);
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+      if (b < nb) {
+        const uint4& w = v[b >> 3];
+        const uint32_t pair = ((b & 7) >> 1) == 0 ? w.x : ((b & 7) >> 1) == 1 ? w.y : ((b & 7) >> 1) == 2 ? w.z : w.w;
+        const uint32_t lv = (b & 1) ? (pair >> 16) : (pair & 0xFFFFu);
+        hk.sample(4 * static_cast<int>(lv), b);
+      }
+    }
+    if ((++words & 31) == 0) hk.poll();
   }
 }
 
@@ -359,7 +399,8 @@ __global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int c
           hk.kmin = &j.kmin[i];
           hk.stop = seg_start;
           const int64_t k_begin = hk.k;
-          replay_segment<Factory>(j, b, i, seg, t0, S, hk);
+          if (j.rec) record_segment(j, i, seg, S, hk);
+          else replay_segment<Factory>(j, b, i, seg, t0, S, hk);
           found = hk.found;
           searched += hk.k - k_begin;
         }
@@ -411,7 +452,8 @@ __global__ void __launch_bounds__(128) summary_kernel(const DevJob j, const int 
       hk.flag = false;
       hk.done = false;
       const int64_t k_begin = hk.k;
-      replay_segment<Factory>(j, b, i, seg, t0, S, hk);
+      if (j.rec) record_segment(j, i, seg, S, hk);
+      else replay_segment<Factory>(j, b, i, seg, t0, S, hk);
       hk.flush();
       atomicMin(&j.summ[i], hk.lo);
       atomicMax(&j.summ[j.p + i], hk.hi);
@@ -468,7 +510,8 @@ __global__ void __launch_bounds__(128) prefix_kernel(const DevJob j, const int c
       const int64_t cut = (k > 0) ? k : M + 1;
       const int64_t seg_first = static_cast<int64_t>(seg) * j.ck_C * j.N + 1;
       PrefixHook hk{b.hist, seg_first - 1, cut, false};
-      replay_segment<Factory>(j, b, i, seg, t0, S, hk);
+      if (j.rec) record_segment(j, i, seg, S, hk);
+      else replay_segment<Factory>(j, b, i, seg, t0, S, hk);
       atomicAdd(&s_samples, static_cast<unsigned long long>(hk.k - (seg_first - 1)));
     }
     asm volatile("" ::: "memory");
@@ -591,7 +634,11 @@ __global__ void __launch_bounds__(128) resolve_kernel(const DevJob j, const int 
         hk.k0 = j.key0;
         hk.k1 = j.key1;
         hk.done = false;
-        replay_chain<Factory>(j, b, i, t0, S, hk);
+        if (j.rec) {
+          for (int sg = 0; sg < j.ck_K && !hk.done; ++sg) record_segment(j, i, sg, S, hk);
+        } else {
+          replay_chain<Factory>(j, b, i, t0, S, hk);
+        }
         j.k[i] = hk.found;
         searched += hk.k;
       }
@@ -657,9 +704,10 @@ inline cudaError_t launch_gen_t(const DevJob& j, const LaunchShape& s, uint64_t 
   const size_t bytes = plan_bytes(j.L, s, TS, true);
   // lattice in shared memory with at most 8 chains a warp: lane groups of 4
   // (groups of 8 for at most 4 chains measured slower at L = 48, 64 and 128)
-  auto kern = gen_kernel<F, TS, 1>;
+  const bool rec = j.rec != nullptr;
+  auto kern = rec ? gen_kernel<F, TS, 1, true> : gen_kernel<F, TS, 1, false>;
   if constexpr (F::kPlacement == kPlaceSmem)
-    if (s.cpw <= 8) kern = gen_kernel<F, TS, 4>;
+    if (s.cpw <= 8) kern = rec ? gen_kernel<F, TS, 4, true> : gen_kernel<F, TS, 4, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
   if (e != cudaSuccess) return e;
   const int per_block = s.cpw * s.wpb;

@@ -58,7 +58,18 @@ struct DevJob {
   int kcap;            // segment capacity
   long long* stats;    // [kStatCount] small device counters
   int32_t* plv;        // [p][M] level after each attempt of a round that is not whole sweeps (nullable)
+  uint16_t* rec;       // [p][M] level after each attempt of the current whole-sweep round, when
+                       // the round is small enough to record (nullable): the joint reads it
+                       // instead of replaying the chains
 };
+
+// whole-sweep rounds of at most this many samples (p * M) record every
+// sample's level (2 bytes each) for the joint -- by default only where the
+// threshold table does not fit in shared memory (L > 64): there a replay
+// is slow and reading the record is faster; at L <= 64 the replays run at
+// generation speed and reading the record measured no faster
+constexpr long long kRecordMax = 1ll << 29;
+inline long long default_record_max(int L) { return L > 64 ? kRecordMax : 0; }
 
 // rounds that are not whole sweeps record every sample's level (for their
 // parallel joint) when p * M is at most this many entries

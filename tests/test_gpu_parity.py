@@ -37,9 +37,13 @@ def _compare_weights(g, o):
 
 
 def _run_parity(L, p, S, iters, start, seed, weights=None, shape=None, M_total=0, order=0, policy=None,
-                seg=None):
+                seg=None, record=None):
     N = L * L
     g = mc.Job(L, p, seed, start)
+    if record is False:
+        g.set_round_record(0)       # the joint replays the chains from checkpoints
+    elif record:
+        g.set_round_record(1 << 29)  # the joint reads the round's record of levels
     if policy is not None:
         g.set_join_policy(*policy)
     if seg is not None:
@@ -93,6 +97,15 @@ def test_weight_iterations_bit_exact(L, p, S, iters, start):
     _run_parity(L, p, S, iters, start, seed=1000 + L)
 
 
+@pytest.mark.parametrize("record", [True, False])
+@pytest.mark.parametrize("L,p,S,iters", [(8, 37, 7, 3), (32, 130, 3, 3), (64, 20, 2, 2), (100, 7, 1, 2),
+                                         (128, 6, 1, 2)])
+def test_weight_iterations_bit_exact_record_and_replay(L, p, S, iters, record):
+    # the joint reading the round's record of levels, and replaying every
+    # sample from the checkpoints (the default depends on L)
+    _run_parity(L, p, S, iters, 1, seed=2000 + L, weights=random_weights(L, L + 3, 6.0), record=record)
+
+
 @pytest.mark.parametrize("L,p,S", [(8, 40, 5), (32, 70, 2), (64, 12, 1)])
 def test_rugged_weight_rejections_and_resolution(L, p, S):
     # a rough weight makes many chains keep nothing, so speculated joint
@@ -127,14 +140,16 @@ def test_energy_ordered_joint_matches_oracle(L, p, S, scale):
     assert list(order) == list(np.lexsort((np.arange(p), lv)))
 
 
+@pytest.mark.parametrize("record", [True, False])
 @pytest.mark.parametrize("policy", [(0, 0, 0), (-1, 0, 0), (0, 0, 64), (-1, 1, 3)])
 @pytest.mark.parametrize("L,p,S", [(8, 40, 3), (32, 70, 2)])
-def test_every_resolution_path_gives_the_serial_rule(policy, L, p, S):
+def test_every_resolution_path_gives_the_serial_rule(policy, L, p, S, record):
     # (0,0,0): no passes, no scan -- the one-block fallback resolves all;
     # (-1,0,0): straight to the summary replay and exact scan;
-    # (0,0,64): speculative passes only; (-1,1,3): one pass, then the scan
+    # (0,0,64): speculative passes only; (-1,1,3): one pass, then the scan;
+    # each reading the round's record of levels, or replaying the chains
     W = random_weights(L, seed=L + 9, scale=10.0)
-    g, o, mism = _run_parity(L, p, S, 3, 1, seed=900 + L, weights=W, policy=policy)
+    g, o, mism = _run_parity(L, p, S, 3, 1, seed=900 + L, weights=W, policy=policy, record=record)
     assert mism > 0
 
 
@@ -156,6 +171,31 @@ def test_segment_lengths_give_the_serial_rule(L, p, S, seg, K, C):
     k = g.k
     M = S * L * L
     assert ((k > C * L * L) & (k <= M)).any()      # some hits beyond the first segment
+
+
+@pytest.mark.parametrize("L,p,S,seg", [(8, 40, 200, 64 * 3), (32, 70, 64, 1024)])
+def test_segment_lengths_with_the_replay_joint(L, p, S, seg):
+    W = random_weights(L, seed=L + 21, scale=10.0)
+    _run_parity(L, p, S, 2, 1, seed=300 + L, weights=W, seg=seg, record=False)
+
+
+def test_round_record_limit_and_memory():
+    L, p, S = 96, 5, 2            # above L = 64 rounds are recorded by default
+    g = mc.Job(L, p, 3, 1)
+    g.run_sweeps(S)
+    g.join()
+    with_rec = g.info()["device_bytes"]
+    assert with_rec == mc.mc_job_device_bytes(L, p, S)
+    h = mc.Job(L, p, 3, 1)
+    h.set_round_record(p * S * L * L - 1)        # one sample too many: replayed
+    h.run_sweeps(S)
+    h.join()
+    assert with_rec - h.info()["device_bytes"] == 2 * p * S * L * L
+    assert np.array_equal(g.k, h.k) and np.array_equal(g.hist, h.hist)
+    with pytest.raises(mc.McError) as e:
+        h.run_sweeps(S)
+        h.set_round_record(0)
+    assert e.value.code == mc.MC_ESTATE
 
 
 def test_segment_length_argument_checks():
