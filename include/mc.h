@@ -116,9 +116,10 @@ int mc_run_attempts(mc_job *job, int64_t n_attempts);
 /* Largest whole-sweep round (p * M samples) whose levels generation records,
  * 2 bytes a sample, for the joint to read instead of replaying the chains
  * from checkpoints (performance and memory only: both give the serial
- * rule's result).  The default is 2^29 for L > 64, where the threshold
- * table does not fit in shared memory and replays are slow, and 0 (no
- * record) for L <= 64; max_samples < 0 restores it, 0 turns the record off.
+ * rule's result).  The default is 2^31 for L >= 64, where reading the
+ * record is faster than replaying, and 0 (no record) below; max_samples < 0
+ * restores it, 0 turns the record off.  The record holds p rounded up to a
+ * multiple of 32 chains.
  * Rounds of mc_batch_run are not recorded.  MC_ESTATE while a round is
  * pending. */
 int mc_set_round_record(mc_job *job, int64_t max_samples);

@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libmcgpu.so")
 SOURCES = ["mc_kernels.cu", "mc_api.cu", "mc_inst_reg_a.cu", "mc_inst_reg_b.cu", "mc_inst_reg_c.cu",
            "mc_inst_smem_1.cu", "mc_inst_smem_2.cu", "mc_inst_smem_3.cu", "mc_inst_smem_4.cu",
            "mc_inst_smem_16.cu", "mc_inst_smem_32.cu", "mc_inst_smem_48.cu", "mc_inst_smem_64.cu", "mc_inst_smem_96.cu", "mc_inst_smem_100.cu",
-           "mc_inst_smem_128.cu", "mc_noalloc.cu", "mc_batch.cu", "mc_server.cu"]
+           "mc_inst_smem_128.cu", "mc_inst_rec.cu", "mc_noalloc.cu", "mc_batch.cu", "mc_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -396,12 +396,14 @@ int ensure_trace(mc_job* job, int64_t n_sweeps) {
   return MC_OK;
 }
 
-// Record buffer for a whole-sweep round of p * M samples (uint16 each), or
-// none when the round is larger than the job's limit (the joint replays).
-int ensure_record(mc_job* job, long long samples, bool allow) {
+// Record buffer for a whole-sweep round of p * M samples (uint16 each, the
+// chains padded to whole tiles of the layout), or none when the round is
+// larger than the job's limit (the joint replays).
+int ensure_record(mc_job* job, int64_t M, bool allow) {
   DevJob& d = job->d;
   d.rec = nullptr;
-  if (!allow || samples > job->rec_max) return MC_OK;
+  if (!allow || static_cast<long long>(job->p) * M > job->rec_max) return MC_OK;
+  const long long samples = mcgpu::rec_entries(job->p, M);
   if (static_cast<size_t>(samples) > job->rec_cap) {
     if (job->rec_buf) {
       raw_free(job, job->rec_buf);
@@ -434,10 +436,11 @@ int round_prepare(mc_job* job, int64_t n_sweeps, uint64_t* t0, bool allow_record
   int K = 0, C = 0;
   round_segments(job->L, job->p, n_sweeps, job->seg_samples, &K, &C);
   if (int rc = ensure_segments(job, K)) return rc;
-  if (int rc = ensure_record(job, static_cast<long long>(job->p) * M, allow_record)) return rc;
+  if (int rc = ensure_record(job, M, allow_record)) return rc;
   DevJob& d = job->d;
   d.ck_K = K;
   d.ck_C = C;
+  d.seg_len = static_cast<int64_t>(C) * job->N;
   const size_t lat = static_cast<size_t>(job->p) * job->L * job->wd;
   MC_CUDA(cudaMemcpyAsync(d.spins0, d.spins, lat * sizeof(uint32_t), cudaMemcpyDeviceToDevice, job->stream),
           "round-start copy");
@@ -1374,7 +1377,9 @@ uint64_t mc_job_device_bytes(int L, int n_chains, int64_t sweeps) {
   round_segments(L, n_chains, sweeps, 0, &K, &C);
   (void)lw;
   const uint64_t samples = p * static_cast<uint64_t>(sweeps) * N;   // record of the round, if small
-  const uint64_t rec = samples <= static_cast<uint64_t>(mcgpu::default_record_max(L)) ? samples * 2 : 0;
+  const uint64_t rec = samples <= static_cast<uint64_t>(mcgpu::default_record_max(L))
+                           ? static_cast<uint64_t>(mcgpu::rec_entries(n_chains, sweeps * static_cast<int64_t>(N))) * 2
+                           : 0;
   return b + static_cast<uint64_t>(K) * bytes_per_segment(L, n_chains) + rec;
 }
 

@@ -270,10 +270,13 @@ __device__ __forceinline__ void sweep_row(uint32_t (&cur)[WD], const uint32_t (&
 // a row; 8 where the row's words already fill the registers.
 //
 // REC: the round is recorded -- every sample's level is also stored, as a
-// uint16, in the chain's row of the record (its samples in order), four
-// samples to one 8-byte store (rows and lattice words hold multiples of
-// four sites, so site b of a word is sample b mod 4 of its group), for the
-// joint to read instead of replaying.
+// uint16, in the round record, four samples to one 8-byte store (rows and
+// lattice words hold multiples of four sites, so site b of a word is sample
+// b mod 4 of its group), for the joint to read instead of replaying.  A
+// chain's consecutive groups of four lie kRecGroupStride entries apart (the
+// 32 chains of a record tile interleaved group by group), so the lanes of a
+// warp with consecutive chains store one contiguous run.
+constexpr int kRecGroupStride = 4 * 32;
 template <int D = 32, bool REC = false>
 struct GenHook {
   uint32_t* hist;
@@ -306,7 +309,7 @@ struct GenHook {
         default:
           pk1 |= lv << 16;
           if (rec_on) *reinterpret_cast<uint2*>(rec) = make_uint2(pk0, pk1);
-          rec += 4;
+          rec += kRecGroupStride;
       }
     }
   }

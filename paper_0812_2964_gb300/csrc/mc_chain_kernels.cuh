@@ -170,6 +170,18 @@ struct RunnerFactorySmem {
   }
 };
 
+// The joint's kernels for a recorded round: levels come from the round
+// record, so there is no lattice to replay and no threshold table (the
+// launch shape's placement only sizes shared memory: none for lattices).
+struct RecF {
+  static constexpr int kPlacement = kPlaceReg;
+};
+template <class F>
+struct IsRec : std::false_type {};
+template <>
+struct IsRec<RecF> : std::true_type {};
+static_assert(kRecGroupStride == 4 * kRecTile, "record layout: generation and joint agree");
+
 // Step 2: every chain performs S sweeps (M = S N attempts) under the current
 // weight; per-level dwell counts accumulate in shared memory, then in the
 // round histogram hgen.  trace[s][c] = energy after sweep s.
@@ -196,10 +208,10 @@ __device__ __forceinline__ void gen_body(const DevJob& j, const int cpw, const u
   hk.init(b.hist, GL == 1 ? 1u : (b.owner ? 1u : 0u), j.np1);
   const bool writer = GL == 1 ? b.active : b.owner;
   if constexpr (REC) {
-    // the chain's row of the record; every lane of a group keeps a valid
+    // the chain's first group in the record; every lane of a group keeps a valid
     // address (pointer arithmetic on a null pointer would let the compiler
     // drop the writer test), only the writer stores
-    hk.rec = j.rec + static_cast<size_t>(b.active ? b.chain : 0) * static_cast<size_t>(S * j.N);
+    hk.rec = j.rec + rec_index(b.active ? b.chain : 0, 0, S * j.N);
     hk.rec_on = writer;
   }
   if (b.active) {
@@ -304,34 +316,42 @@ __device__ __forceinline__ void replay_segment(const DevJob& j, const BlockCtx& 
 }
 
 // The same samples as replay_segment, read from the round's record of
-// levels (generation stored them, one row of M uint16 a chain): a hook sees
-// word(nb) before every 32 samples and sample(4 m, b) for each, in order; no
+// levels (generation stored them, layout rec_index): a hook sees word(nb)
+// before every 32 samples and sample(4 m, b) for each, in order; no
 // Metropolis replay.  The joint uniforms of a hook depend only on the
-// sample's index, so words need not follow lattice rows.  A lane reads its
-// chain's row 16 bytes at a time (segments start on multiples of 16
-// samples, and hold multiples of 16).
+// sample's index, so words need not follow lattice rows.  The next 32
+// samples' groups are loaded while the current ones are tested, so a lane
+// waits on memory once a segment rather than once a word.  (Segments start
+// on multiples of 16 samples and hold multiples of 16.)
 template <class Hook>
 __device__ __forceinline__ void record_segment(const DevJob& j, int i, int seg, int64_t S, Hook& hk) {
-  const int64_t k0 = static_cast<int64_t>(seg) * j.ck_C * j.N;
-  const int64_t k1 = min(S, static_cast<int64_t>(seg + 1) * j.ck_C) * j.N;
-  const uint16_t* row = j.rec + static_cast<size_t>(i) * static_cast<size_t>(S * j.N);
+  const int64_t M = S * j.N;
+  const int64_t k0 = static_cast<int64_t>(seg) * j.seg_len;
+  const int64_t k1 = min(M, k0 + j.seg_len);
+  // group g (samples 4g .. 4g+3) of chain i is grp[g * kRecTile]
+  const uint2* grp = reinterpret_cast<const uint2*>(j.rec + rec_index(i, 0, M));
+  uint2 v[8], nv[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    v[q] = (k0 + 4 * q < k1) ? __ldg(grp + static_cast<size_t>((k0 >> 2) + q) * kRecTile) : make_uint2(0u, 0u);
   int words = 0;
   for (int64_t kb = k0; kb < k1 && !hk.done; kb += 32) {
     const int nb = static_cast<int>(min(static_cast<int64_t>(32), k1 - kb));
-    const uint4* src = reinterpret_cast<const uint4*>(row + kb);
-    uint4 v[4];
+    const int64_t kn = kb + 32;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = (8 * q < nb) ? __ldg(src + q) : make_uint4(0u, 0u, 0u, 0u);
+    for (int q = 0; q < 8; ++q)
+      nv[q] = (kn + 4 * q < k1) ? __ldg(grp + static_cast<size_t>((kn >> 2) + q) * kRecTile) : make_uint2(0u, 0u);
     hk.word(nb);
 #pragma unroll
     for (int b = 0; b < 32; ++b) {
       if (b < nb) {
-        const uint4& w = v[b >> 3];
-        const uint32_t pair = ((b & 7) >> 1) == 0 ? w.x : ((b & 7) >> 1) == 1 ? w.y : ((b & 7) >> 1) == 2 ? w.z : w.w;
+        const uint32_t pair = (b & 2) ? v[b >> 2].y : v[b >> 2].x;
         const uint32_t lv = (b & 1) ? (pair >> 16) : (pair & 0xFFFFu);
         hk.sample(4 * static_cast<int>(lv), b);
       }
     }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = nv[q];
     if ((++words & 31) == 0) hk.poll();
   }
 }
@@ -379,7 +399,7 @@ __global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int c
       const int seg = seg_lo + static_cast<int>(item / nchains);
       const int q = static_cast<int>(item % nchains);
       const int i = list_mode ? list[q] : q;
-      const unsigned long long seg_start = static_cast<unsigned long long>(seg) * j.ck_C * j.N;
+      const unsigned long long seg_start = static_cast<unsigned long long>(seg) * j.seg_len;
       if (__ldcg(&j.kmin[i]) > seg_start) {   // no accepted sample before this segment yet
         const int x = j.xused[i];
         int64_t found;
@@ -389,7 +409,7 @@ __global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int c
           SearchHook hk;
           hk.tj = j.tj + static_cast<size_t>(i) * j.np1;
           hk.k = static_cast<int64_t>(seg_start);
-          hk.M = min(S, static_cast<int64_t>(seg + 1) * j.ck_C) * j.N;
+          hk.M = min(S * j.N, static_cast<int64_t>(seg_start) + j.seg_len);
           hk.found = 0;
           hk.chain = static_cast<uint32_t>(i);
           hk.r = r;
@@ -399,7 +419,7 @@ __global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int c
           hk.kmin = &j.kmin[i];
           hk.stop = seg_start;
           const int64_t k_begin = hk.k;
-          if (j.rec) record_segment(j, i, seg, S, hk);
+          if constexpr (IsRec<Factory>::value) record_segment(j, i, seg, S, hk);
           else replay_segment<Factory>(j, b, i, seg, t0, S, hk);
           found = hk.found;
           searched += hk.k - k_begin;
@@ -440,7 +460,7 @@ __global__ void __launch_bounds__(128) summary_kernel(const DevJob j, const int 
       const int i = j.perm[f + static_cast<int>(item % nchains)];
       SummaryHook hk;
       hk.umin = j.tj + static_cast<size_t>(i) * j.np1;
-      hk.k = static_cast<int64_t>(seg) * j.ck_C * j.N;
+      hk.k = static_cast<int64_t>(seg) * j.seg_len;
       hk.chain = static_cast<uint32_t>(i);
       hk.r = r;
       hk.k0 = j.key0;
@@ -452,7 +472,7 @@ __global__ void __launch_bounds__(128) summary_kernel(const DevJob j, const int 
       hk.flag = false;
       hk.done = false;
       const int64_t k_begin = hk.k;
-      if (j.rec) record_segment(j, i, seg, S, hk);
+      if constexpr (IsRec<Factory>::value) record_segment(j, i, seg, S, hk);
       else replay_segment<Factory>(j, b, i, seg, t0, S, hk);
       hk.flush();
       atomicMin(&j.summ[i], hk.lo);
@@ -483,10 +503,15 @@ struct PrefixHook {
   }
 };
 
+// Discarded prefixes (samples before k_i; the whole chain if nothing is
+// kept) counted into dpre.  Replays take the work list plist of (chain,
+// segment) items; a recorded round takes every (segment, chain) pair,
+// segment-major, and skips those that start at or after the chain's cut.
 template <class Factory, bool TSMEM>
 __global__ void __launch_bounds__(128) prefix_kernel(const DevJob j, const int cpw, const uint64_t t0,
                                                      const int64_t S) {
-  const long long items = j.stats[kStatQueuePrefix];
+  const long long items =
+      IsRec<Factory>::value ? static_cast<long long>(j.p) * j.ck_K : static_cast<long long>(j.stats[kStatQueuePrefix]);
   if (items == 0) return;
   const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, true);
   BlockCtx b = block_setup<TSMEM>(j, sp, cpw, 0, true);
@@ -504,15 +529,18 @@ __global__ void __launch_bounds__(128) prefix_kernel(const DevJob j, const int c
     if (base >= items) break;
     const long long item = base + b.slot;
     if (b.lane < cpw && item < items) {
-      const int2 w = j.plist[item];
+      const int2 w = IsRec<Factory>::value ? make_int2(static_cast<int>(item % j.p), static_cast<int>(item / j.p))
+                                           : j.plist[item];
       const int i = w.x, seg = w.y;
       const int64_t k = j.k[i];
       const int64_t cut = (k > 0) ? k : M + 1;
-      const int64_t seg_first = static_cast<int64_t>(seg) * j.ck_C * j.N + 1;
-      PrefixHook hk{b.hist, seg_first - 1, cut, false};
-      if (j.rec) record_segment(j, i, seg, S, hk);
-      else replay_segment<Factory>(j, b, i, seg, t0, S, hk);
-      atomicAdd(&s_samples, static_cast<unsigned long long>(hk.k - (seg_first - 1)));
+      const int64_t seg_first = static_cast<int64_t>(seg) * j.seg_len + 1;
+      if (seg_first < cut) {
+        PrefixHook hk{b.hist, seg_first - 1, cut, false};
+        if constexpr (IsRec<Factory>::value) record_segment(j, i, seg, S, hk);
+        else replay_segment<Factory>(j, b, i, seg, t0, S, hk);
+        atomicAdd(&s_samples, static_cast<unsigned long long>(hk.k - (seg_first - 1)));
+      }
     }
     asm volatile("" ::: "memory");
     __syncthreads();
@@ -634,7 +662,7 @@ __global__ void __launch_bounds__(128) resolve_kernel(const DevJob j, const int 
         hk.k0 = j.key0;
         hk.k1 = j.key1;
         hk.done = false;
-        if (j.rec) {
+        if constexpr (IsRec<Factory>::value) {
           for (int sg = 0; sg < j.ck_K && !hk.done; ++sg) record_segment(j, i, sg, S, hk);
         } else {
           replay_chain<Factory>(j, b, i, t0, S, hk);
@@ -802,7 +830,8 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
   if ((e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(pbytes))) !=
       cudaSuccess)
     return e;
-  if ((e = join_prefix_list(j, st)) != cudaSuccess) return e;
+  if constexpr (!IsRec<F>::value)
+    if ((e = join_prefix_list(j, st)) != cudaSuccess) return e;
   if ((e = join_reset_queue(j, st)) != cudaSuccess) return e;
   const unsigned grid_pre = static_cast<unsigned>(
       std::min<long long>(blocks_for(items, sp.cpw * sp.wpb), resident_blocks(kp, 32 * sp.wpb, pbytes)));

@@ -53,23 +53,45 @@ struct DevJob {
   // kScanMaxSamples; mc_set_join_policy changes them)
   int passes_scan, passes_plain;
   long long scan_max_samples;
-  int ck_C;            // sweeps per segment in the current round
-  int ck_K;            // segments in the current round
+  int ck_C;            // sweeps per checkpoint segment in the current round
+  int ck_K;            // segments of the joint in the current round
+  int64_t seg_len;     // samples per segment of the joint: ck_C * N for replays from
+                       // checkpoints, shorter for a recorded round (nothing to restore)
   int kcap;            // segment capacity
   long long* stats;    // [kStatCount] small device counters
   int32_t* plv;        // [p][M] level after each attempt of a round that is not whole sweeps (nullable)
-  uint16_t* rec;       // [p][M] level after each attempt of the current whole-sweep round, when
-                       // the round is small enough to record (nullable): the joint reads it
-                       // instead of replaying the chains
+  uint16_t* rec;       // level after each attempt of the current whole-sweep round, when the
+                       // round is small enough to record (nullable; layout: rec_index): the
+                       // joint reads it instead of replaying the chains
 };
 
+// Round record layout: chains in tiles of 32; inside a tile, each group of
+// four consecutive samples of the 32 chains lies side by side, so that a warp
+// of consecutive chains stores (generation) or loads (joint, all chains at
+// the same sample) 256 contiguous bytes per group.  Sample k (0-based) of
+// chain c of a round of M samples (M a multiple of 4) is the uint16 at
+// rec_index(c, k, M); the buffer holds ceil(p / 32) * 32 * M entries.
+constexpr int kRecTile = 32;
+__host__ __device__ inline size_t rec_index(int c, int64_t k, int64_t M) {
+  return ((static_cast<size_t>(c / kRecTile) * static_cast<size_t>(M / 4) + static_cast<size_t>(k >> 2)) *
+              kRecTile +
+          static_cast<size_t>(c % kRecTile)) *
+             4 +
+         static_cast<size_t>(k & 3);
+}
+inline long long rec_entries(int p, int64_t M) {
+  return static_cast<long long>((p + kRecTile - 1) / kRecTile) * kRecTile * M;
+}
+
 // whole-sweep rounds of at most this many samples (p * M) record every
-// sample's level (2 bytes each) for the joint -- by default only where the
-// threshold table does not fit in shared memory (L > 64): there a replay
-// is slow and reading the record is faster; at L <= 64 the replays run at
-// generation speed and reading the record measured no faster
-constexpr long long kRecordMax = 1ll << 29;
-inline long long default_record_max(int L) { return L > 64 ? kRecordMax : 0; }
+// sample's level (2 bytes each, at most 4 GiB) for the joint -- by default
+// from L = 64 on: there reading the record beats replaying from checkpoints
+// by more than the record costs generation (measured at 20 sweeps, 2048
+// chains: L = 64 a weight iteration 11 % shorter, L = 96 16 %, L = 128
+// 32 %); below, replays are as fast as generation and the gain is within a
+// few percent
+constexpr long long kRecordMax = 1ll << 31;
+inline long long default_record_max(int L) { return L >= 64 ? kRecordMax : 0; }
 
 // rounds that are not whole sweeps record every sample's level (for their
 // parallel joint) when p * M is at most this many entries
@@ -158,6 +180,8 @@ MC_CHAIN_UNIT(chain_kernels_smem_L96);
 MC_CHAIN_UNIT(chain_kernels_smem_L100);
 MC_CHAIN_UNIT(chain_kernels_smem_L128);
 #undef MC_CHAIN_UNIT
+// the joint of a recorded round (any L): kernels without lattices or table
+cudaError_t chain_kernels_record(const DevJob& j, uint64_t t0, int64_t S, uint32_t r, cudaStream_t st);
 
 // launch shape chosen by default for (L, p)
 LaunchShape default_shape(int L, int p, int num_sms);

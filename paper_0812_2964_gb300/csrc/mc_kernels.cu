@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(1024) mark_kernel(const DevJob j, const int de
   __syncthreads();
   if (threadIdx.x == 0) {
     const bool deferred = defer && s_count > j.p / 16 &&
-                          static_cast<long long>(s_count) * 11 < static_cast<long long>(j.ck_C) * j.N;
+                          static_cast<long long>(s_count) * 11 < static_cast<long long>(j.seg_len);
     j.stats[kStatPending] = deferred ? 0 : s_count;
     j.stats[kStatFirstPending] = s_first;
     if (s_new) {
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(1024) nohit_kernel(const DevJob j, const int l
   if (threadIdx.x == 0) s_count = 0;
   __syncthreads();
   const int n = list_mode ? static_cast<int>(j.stats[kStatPending]) : j.p;
-  const unsigned long long segN = static_cast<unsigned long long>(j.ck_C) * static_cast<unsigned long long>(j.N);
+  const unsigned long long segN = static_cast<unsigned long long>(j.seg_len);
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
     const int i = list_mode ? j.work[q] : q;
     if (j.kmin[i] > segN) j.work2[atomicAdd(&s_count, 1)] = i;
@@ -834,7 +834,7 @@ __global__ void select_kernel(const DevJob j, const int listed) {
 __global__ void prefix_count_kernel(const DevJob j, const int64_t S) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= j.p) return;
-  const int64_t segN = static_cast<int64_t>(j.ck_C) * j.N;
+  const int64_t segN = j.seg_len;
   const int64_t k = j.k[i];
   const int whole = (k > 0) ? static_cast<int>((k - 1) / segN) : j.ck_K;
   atomicAdd(reinterpret_cast<unsigned long long*>(&j.stats[kStatQueuePrefix]), static_cast<unsigned long long>(whole));
@@ -844,7 +844,7 @@ __global__ void prefix_count_kernel(const DevJob j, const int64_t S) {
 __global__ void prefix_fill_kernel(const DevJob j, const int64_t S) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= j.p) return;
-  const int64_t segN = static_cast<int64_t>(j.ck_C) * j.N;
+  const int64_t segN = j.seg_len;
   const int64_t k = j.k[i];
   const int whole = (k > 0) ? static_cast<int>((k - 1) / segN) : j.ck_K;
   unsigned long long* w = reinterpret_cast<unsigned long long*>(&j.stats[kStatWholeFill]);
@@ -953,6 +953,11 @@ static cudaError_t dispatch(const DevJob& j, const LaunchShape& s, bool gen, uin
 }
 
 cudaError_t k_generate(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S, bool trace, cudaStream_t st) {
+  if (j.rec) {   // a recorded round is never replayed: no checkpoints
+    DevJob g = j;
+    g.ckpt = nullptr;
+    return dispatch(g, s, true, t0, S, trace, 0u, st);
+  }
   return dispatch(j, s, true, t0, S, trace, 0u, st);
 }
 
@@ -965,6 +970,7 @@ cudaError_t k_join(const DevJob& j, const LaunchShape& s, uint64_t t0, int64_t S
     launches_add(3);
     return cudaGetLastError();
   }
+  if (j.rec) return chain_kernels_record(j, t0, S, r, st);   // levels recorded: no replays
   return dispatch(j, join_shape(j.L, s), false, t0, S, false, r, st);
 }
 
