@@ -267,7 +267,7 @@ def job_record(torch, mc, device, workload, S, steps, warmup):
            "config": {"workload": workload, "L": w.L, "chains": w.chains, "sweeps_per_iteration": S,
                       "sweeps_of_the_workload": w.sweeps, "seed": w.seed,
                       "weight_iterations_timed": f"{warmup + 1}..{warmup + steps}",
-                      "launch": {"placement": ["registers", "shared"][info["placement"]],
+                      "launch": {"placement": ["registers", "shared", "global"][info["placement"]],
                                  "chains_per_warp": info["chains_per_warp"],
                                  "warps_per_block": info["warps_per_block"]}},
            "ms_per_step": 1e3 * el / steps, "kept_fraction": kept / (steps * w.chains * M),
@@ -481,7 +481,7 @@ def run_gpu(args):
                    "start": "random" if w.start else "all up", "seed": w.seed,
                    "weight_iterations_timed": f"{args.warmup + 1}..{args.warmup + args.steps}",
                    "l2": "flushed between steps (256 MB write)", "trace": "int32 per sweep",
-                   "launch": {"placement": ["registers", "shared"][info["placement"]],
+                   "launch": {"placement": ["registers", "shared", "global"][info["placement"]],
                               "chains_per_warp": info["chains_per_warp"],
                               "warps_per_block": info["warps_per_block"]},
                    "parallelism": f"replicas x{world}",
@@ -490,7 +490,7 @@ def run_gpu(args):
         "kept_fraction": kept / (args.steps * p * M),
         "raw_attempts_per_s": args.steps * p * M * world / t_max,
         "roofline": {**roof, "traffic": traffic,
-                     "kernel": "gen_kernel (lattice rows in %s)" % ["registers", "shared memory"][info["placement"]],
+                     "kernel": "gen_kernel (lattice rows in %s)" % ["registers", "shared memory", "global memory"][info["placement"]],
                      "measured_issue_active": (issue / 100.0) if issue is not None else None,
                      "measured_issue_lane_weighted": (issue / 100.0 * tr.get("lanes_active", 32) / 32)
                      if issue is not None else None,

@@ -64,7 +64,7 @@ typedef struct mc_info {
   int64_t last_passes;         /* resolution passes of the most recent joint */
   int64_t last_searched;       /* samples replayed while resolving */
   int64_t total_joined;        /* samples kept by all joints of the job */
-  int placement;               /* 0: lattice in registers, 1: in shared memory */
+  int placement;               /* 0: lattice in registers, 1: in shared memory, 2: in global memory */
   int chains_per_warp, warps_per_block;
   size_t device_bytes;         /* device memory held by the job */
   int64_t last_scanned;        /* chains the exact scan settled (0: speculation sufficed) */
@@ -273,9 +273,13 @@ int mc_get_join(mc_job *job, int64_t *k, int64_t *offsets, int n);
 /* Job state and statistics of the last joint.  Synchronises. */
 int mc_get_info(mc_job *job, mc_info *info);
 
-/* Choose how chains map to the GPU (placement 0 = registers, L <= 32;
- * 1 = shared memory), chains per warp 1..32, warps per block 1..4.  The
- * dynamics and all results are independent of this choice. */
+/* Choose how chains map to the GPU (placement 0 = lattice rows in
+ * registers, L <= 32; 1 = shared memory; 2 = global memory with the rows
+ * streamed through registers, L = 96, 100, 128 -- the default there, so that
+ * shared memory holds the threshold table and the histogram; the joint's
+ * replays of such a job use shared memory), chains per warp 1..32, warps
+ * per block 1..4.  The dynamics and all results are independent of this
+ * choice. */
 int mc_set_launch_shape(mc_job *job, int placement, int chains_per_warp, int warps_per_block);
 
 /* `iterations` weight iterations (round of n_sweeps sweeps, joint, weight

@@ -1122,7 +1122,7 @@ static int mc_autotune_impl(mc_job* job, int64_t probe_sweeps, int use_cache, in
     cpws.push_back((job->p + job->num_sms * w - 1) / (job->num_sms * w));
     cpws.push_back((job->p + 2 * sub - 1) / (2 * sub));
   }
-  for (int pl = 0; pl < 2; ++pl)
+  for (int pl = 0; pl < 3; ++pl)
     for (int w = 1; w <= 4; w *= 2)
       for (int c : cpws) {
         LaunchShape s{pl, std::min(32, std::max(1, c)), w};

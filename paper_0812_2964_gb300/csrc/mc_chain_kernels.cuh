@@ -105,6 +105,67 @@ struct SmemRunner {
   }
 };
 
+// Lattice in global memory (the job's spins, updated in place), rows
+// streamed through registers: the row being swept, the one above (swept
+// already in this sweep), the one below, the one after it (loaded two rows
+// ahead, so that the load's latency hides behind two rows of sites) and row
+// 0 as swept in this sweep (the last row's lower neighbour).  Shared memory
+// is left to the threshold table and the histogram: at L = 96 both fit
+// there, which lattices beside them would not allow; at L = 128 more chains
+// share an SM.  The lanes of a lane group store the same words.  Generation
+// only (the joint's replays restore checkpoints into shared memory).
+template <int WD_, int SL>
+struct GlobRunner {
+  static_assert(SL >= 4, "compile-time L");
+  static constexpr int WD = WD_;
+  uint32_t* lat;  // this chain's L rows of WD words
+  __device__ __forceinline__ void load(uint32_t* g) { lat = g; }
+  __device__ __forceinline__ void store(uint32_t* g) const {
+    if (g != lat)
+      for (int i = 0; i < SL * WD; ++i) g[i] = lat[i];
+  }
+  __device__ __forceinline__ void save_strided(uint32_t* __restrict__ g, size_t gstride) const {
+    for (int i = 0; i < SL * WD; ++i) g[i * gstride] = lat[i];
+  }
+  template <bool EARLY, int GL = 1, class Hook>
+  __device__ __forceinline__ void sweep(int& m, Prefetch& pf, const uint32_t* __restrict__ T, int np1,
+                                        uint32_t chain, uint32_t k0, uint32_t k1, Hook& hk) {
+    constexpr int L = SL;
+    uint32_t up[WD], cur[WD], dn[WD], nx[WD], r0[WD];
+#pragma unroll
+    for (int w = 0; w < WD; ++w) {
+      up[w] = lat[(L - 1) * WD + w];
+      cur[w] = lat[w];
+      dn[w] = lat[WD + w];
+      nx[w] = lat[2 * WD + w];
+      r0[w] = 0u;
+    }
+#pragma unroll 1
+    for (int y = 0; y < L; ++y) {
+      sweep_row<WD, GL>(cur, up, dn, L, m, T, np1, pf, chain, k0, k1, hk);
+#pragma unroll
+      for (int w = 0; w < WD; ++w) {
+        lat[y * WD + w] = cur[w];
+        if (y == 0) r0[w] = cur[w];
+        up[w] = cur[w];
+        cur[w] = dn[w];
+        dn[w] = nx[w];
+      }
+      // the row after next: not swept yet in this sweep, or row 0 as swept
+      if (y + 3 < L) {
+#pragma unroll
+        for (int w = 0; w < WD; ++w) nx[w] = lat[(y + 3) * WD + w];
+      } else if (y + 3 == L) {
+#pragma unroll
+        for (int w = 0; w < WD; ++w) nx[w] = r0[w];
+      }
+      if constexpr (EARLY) {
+        if (hk.done) break;
+      }
+    }
+  }
+};
+
 // Shared-memory plan of a block: [table (opt.)][histogram u32][lattices].
 struct SmemPlan {
   int table_words, hist_words, lat_words;
@@ -158,6 +219,10 @@ __device__ __forceinline__ BlockCtx block_setup(const DevJob& j, const SmemPlan&
 template <int L>
 struct RunnerFactoryReg {
   __device__ __forceinline__ static RegRunner<L> make(const BlockCtx&, int) { return RegRunner<L>(); }
+};
+template <int WD, int SL>
+struct RunnerFactoryGlob {
+  __device__ __forceinline__ static GlobRunner<WD, SL> make(const BlockCtx&, int) { return GlobRunner<WD, SL>(); }
 };
 template <int WD, int SL>
 struct RunnerFactorySmem {
@@ -702,6 +767,10 @@ template <int WD, int SL = 0>
 struct SmemF : RunnerFactorySmem<WD, SL> {
   static constexpr int kPlacement = kPlaceSmem;
 };
+template <int WD, int SL>
+struct GlobF : RunnerFactoryGlob<WD, SL> {
+  static constexpr int kPlacement = kPlaceGlobal;
+};
 
 constexpr size_t kMaxSmem = 227 * 1024;
 
@@ -734,7 +803,7 @@ inline cudaError_t launch_gen_t(const DevJob& j, const LaunchShape& s, uint64_t 
   // (groups of 8 for at most 4 chains measured slower at L = 48, 64 and 128)
   const bool rec = j.rec != nullptr;
   auto kern = rec ? gen_kernel<F, TS, 1, true> : gen_kernel<F, TS, 1, false>;
-  if constexpr (F::kPlacement == kPlaceSmem)
+  if constexpr (F::kPlacement != kPlaceReg)
     if (s.cpw <= 8) kern = rec ? gen_kernel<F, TS, 4, true> : gen_kernel<F, TS, 4, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
   if (e != cudaSuccess) return e;
@@ -848,11 +917,23 @@ template <class F>
 struct TableNeverFits : std::false_type {};
 template <int WD, int SL>
 struct TableNeverFits<SmemF<WD, SL>> : std::integral_constant<bool, (SL > 0 && 5ull * 4ull * (SL * SL + 1) > kMaxSmem)> {};
+template <int WD, int SL>
+struct TableNeverFits<GlobF<WD, SL>> : TableNeverFits<SmemF<WD, SL>> {};
+
+template <class F>
+struct IsGlob : std::false_type {};
+template <int WD, int SL>
+struct IsGlob<GlobF<WD, SL>> : std::true_type {};
 
 template <class F>
 inline cudaError_t dispatch_ts(const DevJob& j, const LaunchShape& s, bool gen, uint64_t t0, int64_t S, bool trace,
                                uint32_t r, cudaStream_t st) {
-  if constexpr (TableNeverFits<F>::value) {
+  if constexpr (IsGlob<F>::value) {   // generation only
+    if (!gen) return cudaErrorInvalidValue;
+    if constexpr (TableNeverFits<F>::value) return launch_gen_t<F, false>(j, s, t0, S, trace, st);
+    else return table_fits(j.L, s, true) ? launch_gen_t<F, true>(j, s, t0, S, trace, st)
+                                         : launch_gen_t<F, false>(j, s, t0, S, trace, st);
+  } else if constexpr (TableNeverFits<F>::value) {
     if (gen) return launch_gen_t<F, false>(j, s, t0, S, trace, st);
     return launch_join_t<F, false>(j, s, t0, S, r, st);
   } else {

@@ -11,6 +11,8 @@ namespace mcgpu {
 enum Placement : int {
   kPlaceReg = 0,   // one chain per thread, rows in registers (L <= 32)
   kPlaceSmem = 1,  // one chain per thread, rows in shared memory (any L)
+  kPlaceGlobal = 2,  // one chain per thread, lattice in global memory, rows streamed through
+                     // registers (generation at L = 96, 100, 128; the joint's replays use 1)
 };
 
 struct LaunchShape {

@@ -738,7 +738,8 @@ bool shape_supported(int L, const LaunchShape& s) {
   if (L < 4 || L > 128 || (L % 4) != 0) return false;
   if (s.cpw < 1 || s.cpw > 32 || s.wpb < 1 || s.wpb > 4) return false;
   if (s.placement == kPlaceReg && L > 32) return false;
-  if (s.placement != kPlaceReg && s.placement != kPlaceSmem) return false;
+  if (s.placement == kPlaceGlobal && L != 96 && L != 100 && L != 128) return false;
+  if (s.placement != kPlaceReg && s.placement != kPlaceSmem && s.placement != kPlaceGlobal) return false;
   return plan_bytes(L, s, false, true) <= kMaxSmem;
 }
 
@@ -748,6 +749,9 @@ LaunchShape default_shape(int L, int p, int num_sms) {
   // compile-time shared-memory bodies measured faster (L = 32, 16384 chains:
   // generation 6 % shorter, no rotation of 32 row registers per row)
   s.placement = (L <= 32 && L != 24 && L != 32) ? kPlaceReg : kPlaceSmem;
+  // L = 96, 100, 128: lattices in global memory, shared memory left to the
+  // table (L = 96) and the histogram
+  if (L == 96 || L == 100 || L == 128) s.placement = kPlaceGlobal;
   s.wpb = 4;
   const int warps = std::max(1, num_sms) * 4;  // one warp per SM sub-partition
   s.cpw = std::min(32, std::max(1, (p + warps - 1) / warps));
@@ -788,7 +792,9 @@ static bool replay_fits(int L, const LaunchShape& s) {
   return plan_bytes(L, s, false, false) <= kMaxSmem;
 }
 
-static LaunchShape join_shape(int L, const LaunchShape& gen) {
+static LaunchShape join_shape(int L, const LaunchShape& gen_shape) {
+  LaunchShape gen = gen_shape;
+  if (gen.placement == kPlaceGlobal) gen.placement = kPlaceSmem;   // replays restore into shared memory
   LaunchShape best = gen;
   int best_lanes = 0;
   bool best_ts = false;

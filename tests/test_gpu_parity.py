@@ -125,6 +125,19 @@ def test_launch_shape_large_lattice(shape):
     _run_parity(64, 21, 1, 2, 1, seed=6, shape=shape)
 
 
+@pytest.mark.parametrize("L,p,shape", [(96, 9, (2, 9, 1)), (96, 21, (2, 3, 4)), (100, 7, (2, 7, 1)),
+                                        (128, 6, (2, 2, 3)), (128, 40, (2, 32, 2)),
+                                        (96, 9, (1, 9, 1)), (128, 6, (1, 2, 3))])
+def test_lattice_placement_above_L64(L, p, shape):
+    # placement 2 (the default here): generation with the lattice in global
+    # memory, rows streamed through registers; 1: in shared memory.  Lane
+    # groups of 4 at most 8 chains a warp.  The joint replays in shared memory.
+    _run_parity(L, p, 1, 2, 1, seed=40 + L, shape=shape, weights=random_weights(L, L + 1, 6.0))
+    g = mc.Job(L, p, 1, 1)
+    g.set_launch_shape(*shape)
+    assert g.info()["placement"] == shape[0]
+
+
 def test_rounds_until_M_total():
     _run_parity(16, 20, 2, 3, 1, seed=9, M_total=int(2.5 * 20 * 2 * 256))
 
