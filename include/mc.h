@@ -275,11 +275,11 @@ int mc_get_info(mc_job *job, mc_info *info);
 
 /* Choose how chains map to the GPU (placement 0 = lattice rows in
  * registers, L <= 32; 1 = shared memory; 2 = global memory with the rows
- * streamed through registers, L = 96, 100, 128 -- the default there, so that
- * shared memory holds the threshold table and the histogram; the joint's
- * replays of such a job use shared memory), chains per warp 1..32, warps
- * per block 1..4.  The dynamics and all results are independent of this
- * choice. */
+ * streamed through registers, L = 96, 100, 128 -- the default at L = 96,
+ * where the threshold table then fits in shared memory, and with more than
+ * 8 chains a warp at L = 100, 128; the joint's replays of such a job use
+ * shared memory), chains per warp 1..32, warps per block 1..4.  The
+ * dynamics and all results are independent of this choice. */
 int mc_set_launch_shape(mc_job *job, int placement, int chains_per_warp, int warps_per_block);
 
 /* `iterations` weight iterations (round of n_sweeps sweeps, joint, weight

@@ -234,7 +234,7 @@ static int mc_init_impl(int L, int n_chains, uint64_t seed, int start, mc_job** 
       (rc = dalloc(j, &d.xused, n_chains)) || (rc = dalloc(j, &d.tj, static_cast<size_t>(n_chains) * np1)) ||
       (rc = dalloc(j, &d.offsets, n_chains)) || (rc = dalloc(j, &d.work, n_chains)) ||
       (rc = dalloc(j, &d.work2, n_chains)) ||
-      (rc = dalloc(j, &d.lastacc, n_chains)) || (rc = dalloc(j, &d.summ, 3ull * n_chains)) || (rc = dalloc(j, &d.visited, np1)) ||
+      (rc = dalloc(j, &d.lastacc, n_chains)) || (rc = dalloc(j, &d.summ, 5ull * n_chains)) || (rc = dalloc(j, &d.visited, np1)) ||
       (rc = dalloc(j, &d.perm, n_chains)) || (rc = dalloc(j, &d.lvcnt, np1)) || (rc = dalloc(j, &d.kmin, n_chains)) ||
       (rc = dalloc(j, &d.stats, mcgpu::kStatCount))) {
     free_all(j);
@@ -1372,7 +1372,7 @@ uint64_t mc_job_device_bytes(int L, int n_chains, int64_t sweeps) {
   // as allocated by mc_init: spins, spins0, m, m0, W, T, h, hgen, dpre, k,
   // xused, tj, offsets, work, work2, lastacc, summ, visited, perm, lvcnt, kmin, stats
   uint64_t b = lat * 4 * 2 + p * 4 * 2 + np1 * 8 + 5 * np1 * 4 + np1 * 8 * 3 + p * 8 + p * 4 + p * np1 * 4 +
-               p * 8 + p * 4 + p * 4 + p * 4 + p * 12 + np1 + p * 4 + np1 * 4 + p * 8 + mcgpu::kStatCount * 8;
+               p * 8 + p * 4 + p * 4 + p * 4 + p * 20 + np1 + p * 4 + np1 * 4 + p * 8 + mcgpu::kStatCount * 8;
   int K = 0, C = 0;
   round_segments(L, n_chains, sweeps, 0, &K, &C);
   (void)lw;

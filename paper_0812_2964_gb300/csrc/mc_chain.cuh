@@ -376,6 +376,14 @@ struct SearchHook {
 // of a segment, the smallest joint uniform seen at each level, folded into
 // the chain's row with atomicMin once per run of equal levels; also the
 // range of levels visited and whether some run's minimum was 0xFFFFFFFF.
+// W > 0: the runs' minima first go to this lane's window of W levels in
+// shared memory (column win, stride kWinStride; placed around the first
+// level seen, every entry 0xFFFFFFFF on entry and again after drain()), and
+// drain() folds the window into the row once a segment -- one global atomic
+// per level visited instead of one per run (levels outside the window go to
+// the row directly).
+constexpr int kWinStride = 128;
+template <int W = 0>
 struct SummaryHook {
   uint32_t* umin;  // row of the chain, indexed by level
   int64_t k;
@@ -385,6 +393,34 @@ struct SummaryHook {
   uint32_t run_min;
   bool flag;
   bool done;       // never set: the whole segment is summarised
+  uint32_t* win = nullptr;
+  int base = kNoBase;
+  static constexpr int kNoBase = -0x7FFFFFFF;
+  __device__ __forceinline__ void put(int m, uint32_t v) {
+    if constexpr (W > 0) {
+      if (base == kNoBase) base = m - W / 2;
+      const unsigned s = static_cast<unsigned>(m - base);
+      if (s < static_cast<unsigned>(W)) {
+        uint32_t* e = win + s * kWinStride;
+        *e = min(*e, v);
+        return;
+      }
+    }
+    atomicMin(&umin[m], v);
+  }
+  __device__ __forceinline__ void drain() {
+    if constexpr (W > 0) {
+      if (base == kNoBase) return;
+      for (int s = 0; s < W; ++s) {
+        const uint32_t v = win[s * kWinStride];
+        if (v != 0xFFFFFFFFu) {
+          atomicMin(&umin[base + s], v);
+          win[s * kWinStride] = 0xFFFFFFFFu;
+        }
+      }
+      base = kNoBase;
+    }
+  }
   __device__ __forceinline__ void poll() {}
   __device__ __forceinline__ void word(int nb) { joint_fill(uj, nb, k, r, chain, k0, k1); }
   __device__ __forceinline__ void sample(int m4, int b) {
@@ -401,7 +437,7 @@ struct SummaryHook {
   }
   __device__ __forceinline__ void flush() {
     if (cur >= 0) {
-      atomicMin(&umin[cur], run_min);
+      put(cur, run_min);
       flag = flag || (run_min == 0xFFFFFFFFu);
       lo = min(lo, cur);
       hi = max(hi, cur);

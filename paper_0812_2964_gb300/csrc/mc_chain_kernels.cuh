@@ -511,6 +511,11 @@ __global__ void __launch_bounds__(128) summary_kernel(const DevJob j, const int 
   const long long items = static_cast<long long>(nchains) * j.ck_K;
   const SmemPlan sp = smem_plan(j.L, Factory::kPlacement, cpw, blockDim.x >> 5, TSMEM, false);
   BlockCtx b = block_setup<TSMEM>(j, sp, cpw, 0, false);
+  // a recorded round: every lane keeps a window of levels in shared memory
+  constexpr int W = IsRec<Factory>::value ? 64 : 0;
+  __shared__ uint32_t s_win[W > 0 ? W * kWinStride : 1];
+  if constexpr (W > 0)
+    for (int q = threadIdx.x; q < W * kWinStride; q += blockDim.x) s_win[q] = 0xFFFFFFFFu;
   __syncthreads();
   unsigned long long* queue = reinterpret_cast<unsigned long long*>(&j.stats[kStatQueueSearch]);
   long long searched = 0;
@@ -523,7 +528,8 @@ __global__ void __launch_bounds__(128) summary_kernel(const DevJob j, const int 
     if (b.lane < cpw && item < items) {
       const int seg = static_cast<int>(item / nchains);
       const int i = j.perm[f + static_cast<int>(item % nchains)];
-      SummaryHook hk;
+      SummaryHook<W> hk;
+      if constexpr (W > 0) hk.win = s_win + threadIdx.x;
       hk.umin = j.tj + static_cast<size_t>(i) * j.np1;
       hk.k = static_cast<int64_t>(seg) * j.seg_len;
       hk.chain = static_cast<uint32_t>(i);
@@ -540,6 +546,7 @@ __global__ void __launch_bounds__(128) summary_kernel(const DevJob j, const int 
       if constexpr (IsRec<Factory>::value) record_segment(j, i, seg, S, hk);
       else replay_segment<Factory>(j, b, i, seg, t0, S, hk);
       hk.flush();
+      hk.drain();
       atomicMin(&j.summ[i], hk.lo);
       atomicMax(&j.summ[j.p + i], hk.hi);
       if (hk.flag) atomicOr(&j.summ[2 * j.p + i], 1);

@@ -46,7 +46,8 @@ struct DevJob {
   int32_t* ckm;        // [kcap][p] level at the start of each round segment
   unsigned long long* kmin;  // [p] earliest accepted sample found so far for the chain's input (kNoHit: none)
   int2* plist;         // [p*kcap] (chain, segment) work list of the prefix pass
-  int32_t* summ;       // [3][p] summary pass: lowest and highest level visited, flag
+  int32_t* summ;       // [5][p] summary pass: lowest and highest level visited, flag; then
+                       // [p][8] bytes: the exact scan's answers for candidate inputs
   uint8_t* visited;    // [np1] 1 once a weight update has seen h > 0 at the level
   int32_t* perm;       // [p] chain at each position of the joint (identity unless ordered)
   int32_t* lvcnt;      // [np1] scratch of the energy ordering

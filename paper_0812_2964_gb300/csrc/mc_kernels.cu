@@ -378,8 +378,11 @@ __global__ void __launch_bounds__(1024) mark_kernel(const DevJob j, const int de
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    // (a recorded round's summary reads the record and the scan mostly
+    // looks its answers up: whenever a sixteenth of the chains wait, it is
+    // the shorter way)
     const bool deferred = defer && s_count > j.p / 16 &&
-                          static_cast<long long>(s_count) * 11 < static_cast<long long>(j.seg_len);
+                          (j.rec != nullptr || static_cast<long long>(s_count) * 11 < static_cast<long long>(j.seg_len));
     j.stats[kStatPending] = deferred ? 0 : s_count;
     j.stats[kStatFirstPending] = s_first;
     if (s_new) {
@@ -421,60 +424,121 @@ __global__ void summary_init_kernel(const DevJob j) {
 // answer the summary cannot give (a level whose every uniform was
 // 0xFFFFFFFF, against a threshold of 0xFFFFFFFF) stops the scan; the chains
 // from it on keep their speculated inputs for the ordinary passes.
+//
+// Most inputs the scan meets are the last level of one of the few chains
+// just before (the rest of them kept nothing): cand_kernel settles, in
+// parallel and in the same way, chain q under the input of each of the
+// kScanCand positions before it (position -1: the carry), and the scan
+// looks those answers up; only an input from further back is evaluated in
+// the scan itself.
+constexpr int kScanCand = 8;
+
+__device__ __forceinline__ uint8_t* scan_cand(const DevJob& j) {
+  return reinterpret_cast<uint8_t*>(j.summ + 3 * static_cast<size_t>(j.p));   // [p][kScanCand]
+}
+
+// Whether the chain at joint position pos keeps samples for input level
+// x >= 0, from its summary: 1 yes, 0 no, 2 undecidable (a level whose every
+// uniform was 0xFFFFFFFF, against a threshold of 0xFFFFFFFF).  Warp-
+// collective: the 32 lanes call it with the same arguments.
+__device__ __forceinline__ int scan_decide(const DevJob& j, int pos, int x) {
+  const int lane = threadIdx.x & 31;
+  const int ch = j.perm[pos];
+  const uint32_t* um = j.tj + static_cast<size_t>(ch) * j.np1;
+  const double wx = j.W[x];
+  const bool flag = j.summ[2 * j.p + ch] != 0;
+  int hit = 0, amb = 0;
+  for (int m = j.summ[ch] + lane; m <= j.summ[j.p + ch]; m += 32) {
+    const uint32_t u = um[m];
+    if (u != 0xFFFFFFFFu || flag) {
+      const uint32_t thr = threshold_det(__dsub_rn(j.W[m], wx));
+      if (u != 0xFFFFFFFFu) hit |= (u <= thr) ? 1 : 0;
+      else amb |= (thr == 0xFFFFFFFFu) ? 1 : 0;
+    }
+  }
+  hit = __any_sync(0xFFFFFFFFu, hit);
+  amb = __any_sync(0xFFFFFFFFu, amb);
+  return hit ? 1 : (amb ? 2 : 0);
+}
+
+// answer codes: those of scan_decide, 3 not evaluated
+__global__ void __launch_bounds__(256) cand_kernel(const DevJob j) {
+  if (j.stats[kStatPending] == 0) return;
+  const int f = static_cast<int>(j.stats[kStatFirstPending]);
+  const int carry_in = j.stats[kStatCarryValid] ? static_cast<int>(j.stats[kStatCarry]) : -1;
+  uint8_t* cand = scan_cand(j);
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+  const long long n = static_cast<long long>(j.p - f) * kScanCand;
+  for (long long w = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5; w < n; w += nwarps) {
+    const int q = f + static_cast<int>(w / kScanCand), d = 1 + static_cast<int>(w % kScanCand);
+    const int src = q - d;
+    const int x = src >= 0 ? j.m[j.perm[src]] : (src == -1 ? carry_in : -1);
+    const int code = x >= 0 ? scan_decide(j, q, x) : 3;
+    if (lane == 0) cand[static_cast<size_t>(q) * kScanCand + d - 1] = static_cast<uint8_t>(code);
+  }
+}
+
+// The loop over chains is serial and runs in one warp; the block's other
+// warps only stage each chunk of chains into shared memory.
 __global__ void __launch_bounds__(1024) scan_kernel(const DevJob j) {
   if (j.stats[kStatPending] == 0) return;
   constexpr int kChunk = 1024;
-  __shared__ int s_xu[kChunk], s_m[kChunk], s_lo[kChunk], s_hi[kChunk];
-  __shared__ signed char s_ks[kChunk], s_fl[kChunk];
-  __shared__ int s_count;
+  __shared__ int s_xu[kChunk], s_m[kChunk], s_ch[kChunk];
+  __shared__ signed char s_ks[kChunk];
+  __shared__ uint8_t s_cand[kChunk * kScanCand];
+  __shared__ int s_count, s_stop;
   const int t = threadIdx.x, nt = blockDim.x;
   const int f = static_cast<int>(j.stats[kStatFirstPending]);
   const int carry_in = j.stats[kStatCarryValid] ? static_cast<int>(j.stats[kStatCarry]) : -1;
-  int x = (j.lastacc[f] >= 0) ? j.m[j.perm[j.lastacc[f]]] : carry_in;
-  if (t == 0) s_count = 0;
-  int i = f, scanned = 0;   // i: position in the joint
-  bool stopped = false;
-  for (int c0 = f; c0 < j.p && !stopped; c0 += kChunk) {
+  const uint8_t* cand = scan_cand(j);
+  int last = j.lastacc[f];   // position of the nearest chain before that kept samples (-1: none)
+  int x = (last >= 0) ? j.m[j.perm[last]] : carry_in;
+  if (t == 0) {
+    s_count = 0;
+    s_stop = 0;
+  }
+  int i = f, scanned = 0;   // i: position in the joint (the serial warp's)
+  for (int c0 = f; c0 < j.p; c0 += kChunk) {
     const int n = min(kChunk, j.p - c0);
     __syncthreads();
+    if (s_stop) break;
     for (int q = t; q < n; q += nt) {
       const int c = j.perm[c0 + q];
       const int64_t kc = j.k[c];
+      s_ch[q] = c;
       s_xu[q] = j.xused[c];
       s_ks[q] = kc > 0 ? 1 : (kc == 0 ? 0 : -1);
       s_m[q] = j.m[c];
-      s_lo[q] = j.summ[c];
-      s_hi[q] = j.summ[j.p + c];
-      s_fl[q] = j.summ[2 * j.p + c] ? 1 : 0;
     }
+    for (int q = t; q < n * kScanCand; q += nt) s_cand[q] = cand[static_cast<size_t>(c0) * kScanCand + q];
     __syncthreads();
+    if (t >= 32) continue;
+    bool stopped = false;
     for (int q = 0; q < n; ++q) {
       i = c0 + q;
-      const int ch = j.perm[i];
+      const int ch = s_ch[q];
       const bool known = (x == s_xu[q] && s_ks[q] >= 0);
       bool acc;
       if (known) {
         acc = s_ks[q] > 0;
       } else if (x < 0) {
         acc = true;  // no input yet: the chain is kept whole (k = 1)
-      } else {
-        const uint32_t* um = j.tj + static_cast<size_t>(ch) * j.np1;
-        const double wx = j.W[x];
-        const bool flag = s_fl[q] != 0;
-        int hit = 0, amb = 0;
-        for (int m = s_lo[q] + t; m <= s_hi[q]; m += nt) {
-          const uint32_t u = um[m];
-          if (u != 0xFFFFFFFFu || flag) {
-            const uint32_t thr = threshold_det(__dsub_rn(j.W[m], wx));
-            if (u != 0xFFFFFFFFu) hit |= (u <= thr) ? 1 : 0;
-            else amb |= (thr == 0xFFFFFFFFu) ? 1 : 0;
-          }
-        }
-        acc = __syncthreads_or(hit) != 0;
-        if (!acc && __syncthreads_or(amb)) {
+      } else if (i - last <= kScanCand && s_cand[q * kScanCand + (i - last - 1)] < 3) {
+        const int code = s_cand[q * kScanCand + (i - last - 1)];   // the input came from i - last positions back
+        if (code == 2) {
           stopped = true;
           break;
         }
+        acc = code == 1;
+        ++scanned;
+      } else {
+        const int code = scan_decide(j, i, x);   // an input from further back
+        if (code == 2) {
+          stopped = true;
+          break;
+        }
+        acc = code == 1;
         ++scanned;
       }
       if (!known) {
@@ -491,9 +555,16 @@ __global__ void __launch_bounds__(1024) scan_kernel(const DevJob j) {
         }
         if (acc && x >= 0 && t == 0) j.kmin[ch] = kNoHit;
       }
-      if (acc) x = s_m[q];
+      if (acc) {
+        x = s_m[q];
+        last = i;
+      }
     }
-    if (!stopped) i = c0 + n;
+    if (stopped) {
+      if (t == 0) s_stop = 1;
+    } else {
+      i = c0 + n;
+    }
   }
   __syncthreads();
   // stopped early: chains still waiting for a search keep their inputs
@@ -749,12 +820,15 @@ LaunchShape default_shape(int L, int p, int num_sms) {
   // compile-time shared-memory bodies measured faster (L = 32, 16384 chains:
   // generation 6 % shorter, no rotation of 32 row registers per row)
   s.placement = (L <= 32 && L != 24 && L != 32) ? kPlaceReg : kPlaceSmem;
-  // L = 96, 100, 128: lattices in global memory, shared memory left to the
-  // table (L = 96) and the histogram
-  if (L == 96 || L == 100 || L == 128) s.placement = kPlaceGlobal;
   s.wpb = 4;
   const int warps = std::max(1, num_sms) * 4;  // one warp per SM sub-partition
   s.cpw = std::min(32, std::max(1, (p + warps - 1) / warps));
+  // lattices in global memory: at L = 96 so that the threshold table fits in
+  // shared memory (generation 2.2x faster at 1024 and 2048 chains, 20
+  // sweeps); at L = 100, 128 (table in global memory either way) only with
+  // full warps, where they leave a block's shared memory to the histogram --
+  // lane groups ran 6-9 % faster with the lattices in shared memory
+  if (L == 96 || ((L == 100 || L == 128) && s.cpw > 8)) s.placement = kPlaceGlobal;
   while (s.wpb > 1 && !shape_supported(L, s)) s.wpb >>= 1;
   while (s.cpw > 1 && !shape_supported(L, s)) s.cpw >>= 1;
   return s;
@@ -767,7 +841,11 @@ LaunchShape default_shape(int L, int p, int num_sms) {
 // a job shaped this way takes the same time on far fewer warps -- the rest
 // of the GPU stays free for other jobs (the server uses it).
 LaunchShape dense_shape(int L, int p, int num_sms) {
-  const LaunchShape def = default_shape(L, p, num_sms);
+  LaunchShape def = default_shape(L, p, num_sms);
+  // full warps at L = 100, 128 keep their lattices in global memory: a block
+  // of 128 chains then needs only the histogram's shared memory, so blocks
+  // of other jobs fit beside it
+  if (L == 100 || L == 128) def.placement = kPlaceGlobal;
   const bool ts = table_fits(L, def, true);
   for (int cpw = std::min(32, std::max(1, p)); cpw >= 1; --cpw)
     for (int w = 4; w >= 1; --w) {
@@ -882,8 +960,10 @@ cudaError_t join_summary_init(const DevJob& j, cudaStream_t st) {
 }
 
 cudaError_t join_scan(const DevJob& j, cudaStream_t st) {
+  // one warp per (chain, candidate input), grid-stride
+  cand_kernel<<<std::min(1024u, blocks_for(static_cast<long long>(j.p) * kScanCand * 32, 256)), 256, 0, st>>>(j);
   scan_kernel<<<1, 1024, 0, st>>>(j);
-  launches_add(1);
+  launches_add(2);
   return cudaGetLastError();
 }
 

@@ -91,15 +91,28 @@ int run(int L, int p, int64_t S, uint64_t seed, const double* W, int start) {
       const int64_t k_or = or_chain_first_accept(L, seed, (uint32_t)c, 0, S, Tor.data(), W, s0.data(), m_or, x, r,
                                                  nullptr);
       std::vector<uint32_t> umin(np1, 0xFFFFFFFFu);
-      SummaryHook su;
+      SummaryHook<> su;
       su.umin = umin.data(); su.k = 0; su.chain = (uint32_t)c; su.r = r; su.k0 = (uint32_t)seed;
       su.k1 = (uint32_t)(seed >> 32); su.cur = -1; su.lo = 0x7FFFFFFF; su.hi = -1; su.run_min = 0xFFFFFFFFu;
       su.flag = false; su.done = false;
       replay<WD>(L, S, lat0, m_or, T.data(), np1, seed, (uint32_t)c, su, false);
       su.flush();
+      // the same summary through a window of 8 levels (most levels fall
+      // outside it, so both paths run): the same row once drained, and the
+      // window empty again
+      std::vector<uint32_t> umin_w(np1, 0xFFFFFFFFu), win(8 * kWinStride, 0xFFFFFFFFu);
+      SummaryHook<8> sw;
+      sw.umin = umin_w.data(); sw.k = 0; sw.chain = (uint32_t)c; sw.r = r; sw.k0 = (uint32_t)seed;
+      sw.k1 = (uint32_t)(seed >> 32); sw.cur = -1; sw.lo = 0x7FFFFFFF; sw.hi = -1; sw.run_min = 0xFFFFFFFFu;
+      sw.flag = false; sw.done = false; sw.win = win.data() + 5;
+      replay<WD>(L, S, lat0, m_or, T.data(), np1, seed, (uint32_t)c, sw, false);
+      sw.flush();
+      sw.drain();
+      bool win_ok = umin_w == umin && sw.lo == su.lo && sw.hi == su.hi && sw.flag == su.flag;
+      for (uint32_t v : win) win_ok = win_ok && v == 0xFFFFFFFFu;
       bool acc = false;
       for (int q = su.lo; q <= su.hi; ++q) acc = acc || (umin[q] != 0xFFFFFFFFu && umin[q] <= tj[q]);
-      if (sh.found != k_or || acc != (k_or > 0) || su.k != S * N) {
+      if (sh.found != k_or || acc != (k_or > 0) || su.k != S * N || !win_ok) {
         ++bad;
         if (bad < 3) printf("L=%d chain %d joint hooks: search %lld vs %lld, summary %d\n", L, c,
                             (long long)sh.found, (long long)k_or, (int)acc);
