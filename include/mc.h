@@ -116,8 +116,7 @@ int mc_run_attempts(mc_job *job, int64_t n_attempts);
 /* Largest whole-sweep round (p * M samples) whose levels generation records,
  * 2 bytes a sample, for the joint to read instead of replaying the chains
  * from checkpoints (performance and memory only: both give the serial
- * rule's result).  The default is 2^31 for L >= 64, where reading the
- * record is faster than replaying, and 0 (no record) below; max_samples < 0
+ * rule's result).  The default is 2^33 (16 GiB of record); max_samples < 0
  * restores it, 0 turns the record off.  The record holds p rounded up to a
  * multiple of 32 chains.
  * Rounds of mc_batch_run are not recorded.  MC_ESTATE while a round is

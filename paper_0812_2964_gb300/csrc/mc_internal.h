@@ -87,14 +87,15 @@ inline long long rec_entries(int p, int64_t M) {
 }
 
 // whole-sweep rounds of at most this many samples (p * M) record every
-// sample's level (2 bytes each, at most 4 GiB) for the joint -- by default
-// from L = 64 on: there reading the record beats replaying from checkpoints
-// by more than the record costs generation (measured at 20 sweeps, 2048
-// chains: L = 64 a weight iteration 11 % shorter, L = 96 16 %, L = 128
-// 32 %); below, replays are as fast as generation and the gain is within a
-// few percent
-constexpr long long kRecordMax = 1ll << 31;
-inline long long default_record_max(int L) { return L >= 64 ? kRecordMax : 0; }
+// sample's level (2 bytes each, at most 16 GiB) for the joint: reading the
+// record beats replaying from checkpoints by more than the record costs
+// generation (weight iterations measured on GB300, record against replay:
+// 20 sweeps and 2048 chains, L = 16 15 % shorter, 32 20 %, 48 14 %, 64 20 %,
+// 96 19 %, 128 34 %; L = 32, 16384 chains 15 %; L = 64, 4096 chains, 100
+// sweeps 29 %; L = 96, 200 sweeps 32 %; L = 128, 1024 chains, 400 sweeps
+// 13 %)
+constexpr long long kRecordMax = 1ll << 33;
+inline long long default_record_max(int /*L*/) { return kRecordMax; }
 
 // rounds that are not whole sweeps record every sample's level (for their
 // parallel joint) when p * M is at most this many entries

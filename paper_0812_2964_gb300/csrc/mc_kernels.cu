@@ -427,10 +427,13 @@ __global__ void summary_init_kernel(const DevJob j) {
 //
 // Most inputs the scan meets are the last level of one of the few chains
 // just before (the rest of them kept nothing): cand_kernel settles, in
-// parallel and in the same way, chain q under the input of each of the
-// kScanCand positions before it (position -1: the carry), and the scan
-// looks those answers up; only an input from further back is evaluated in
-// the scan itself.
+// parallel, chain q under the input of each of the kScanCand positions
+// before it (position -1: the carry).  The serial rule then becomes a small
+// state machine over positions -- state d = how many positions back the
+// current input came from -- whose per-position transition functions are
+// composed by a block-wide prefix scan, so the scan costs O(p / 1024) and
+// not O(p); only an input from further back than kScanCand positions is
+// evaluated one chain at a time.
 constexpr int kScanCand = 8;
 
 __device__ __forceinline__ uint8_t* scan_cand(const DevJob& j) {
@@ -461,7 +464,9 @@ __device__ __forceinline__ int scan_decide(const DevJob& j, int pos, int x) {
   return hit ? 1 : (amb ? 2 : 0);
 }
 
-// answer codes: those of scan_decide, 3 not evaluated
+// Answer codes: 0 keeps nothing, 1 keeps samples, 2 undecidable (the scan
+// stops there), 3 no such input, 4 / 5 as 0 / 1 but k is already known for
+// this input (nothing to write).
 __global__ void __launch_bounds__(256) cand_kernel(const DevJob j) {
   if (j.stats[kStatPending] == 0) return;
   const int f = static_cast<int>(j.stats[kStatFirstPending]);
@@ -474,105 +479,191 @@ __global__ void __launch_bounds__(256) cand_kernel(const DevJob j) {
     const int q = f + static_cast<int>(w / kScanCand), d = 1 + static_cast<int>(w % kScanCand);
     const int src = q - d;
     const int x = src >= 0 ? j.m[j.perm[src]] : (src == -1 ? carry_in : -1);
-    const int code = x >= 0 ? scan_decide(j, q, x) : 3;
+    int code = 3;
+    if (x >= 0) {
+      const int ch = j.perm[q];
+      const int64_t kc = j.k[ch];
+      code = (kc >= 0 && j.xused[ch] == x) ? (kc > 0 ? 5 : 4) : scan_decide(j, q, x);
+    }
     if (lane == 0) cand[static_cast<size_t>(q) * kScanCand + d - 1] = static_cast<uint8_t>(code);
   }
 }
 
-// The loop over chains is serial and runs in one warp; the block's other
-// warps only stage each chunk of chains into shared memory.
+// Scan states: 0 no input yet (the chain is kept whole), d = 1..8 the input
+// is the last level of the chain d positions back, kFar from further back,
+// kStop undecidable.  A transition function holds the next state of every
+// state in 4-bit fields.
+constexpr int kFar = 9, kStop = 10, kStates = 11;
+using Trans = unsigned long long;
+
+__device__ __forceinline__ int tr_at(Trans T, int s) { return static_cast<int>((T >> (4 * s)) & 15u); }
+
+__device__ __forceinline__ Trans tr_identity() {
+  Trans r = 0;
+#pragma unroll
+  for (int s = 0; s < kStates; ++s) r |= static_cast<Trans>(s) << (4 * s);
+  return r;
+}
+
+// B after A
+__device__ __forceinline__ Trans tr_then(Trans A, Trans B) {
+  Trans r = 0;
+#pragma unroll
+  for (int s = 0; s < kStates; ++s) r |= static_cast<Trans>(tr_at(B, tr_at(A, s))) << (4 * s);
+  return r;
+}
+
+// the transition of a position from its answer codes (one byte per d)
+__device__ __forceinline__ Trans tr_position(unsigned long long codes) {
+  Trans r = static_cast<Trans>(1) | (static_cast<Trans>(kFar) << (4 * kFar)) |
+            (static_cast<Trans>(kStop) << (4 * kStop));
+#pragma unroll
+  for (int d = 1; d <= kScanCand; ++d) {
+    const int c = static_cast<int>((codes >> (8 * (d - 1))) & 0xFFu);
+    const int next = (c == 1 || c == 5) ? 1 : (c == 0 || c == 4) ? (d == kScanCand ? kFar : d + 1) : kStop;
+    r |= static_cast<Trans>(next) << (4 * d);
+  }
+  return r;
+}
+
+__device__ __forceinline__ unsigned long long cand_codes(const DevJob& j, int q) {
+  const uint32_t* c32 = reinterpret_cast<const uint32_t*>(scan_cand(j));
+  const size_t w = 2 * static_cast<size_t>(q);
+  return c32[w] | (static_cast<unsigned long long>(c32[w + 1]) << 32);
+}
+
 __global__ void __launch_bounds__(1024) scan_kernel(const DevJob j) {
   if (j.stats[kStatPending] == 0) return;
-  constexpr int kChunk = 1024;
-  __shared__ int s_xu[kChunk], s_m[kChunk], s_ch[kChunk];
-  __shared__ signed char s_ks[kChunk];
-  __shared__ uint8_t s_cand[kChunk * kScanCand];
-  __shared__ int s_count, s_stop;
+  static_assert(kScanCand == 8 && kStates <= 16, "answer codes in one 64-bit word, states in 4 bits");
+  __shared__ Trans s_tr[1024];
+  __shared__ int s_first, s_count, s_state, s_from, s_last, s_end;
+  __shared__ unsigned long long s_scanned;
   const int t = threadIdx.x, nt = blockDim.x;
   const int f = static_cast<int>(j.stats[kStatFirstPending]);
   const int carry_in = j.stats[kStatCarryValid] ? static_cast<int>(j.stats[kStatCarry]) : -1;
-  const uint8_t* cand = scan_cand(j);
-  int last = j.lastacc[f];   // position of the nearest chain before that kept samples (-1: none)
-  int x = (last >= 0) ? j.m[j.perm[last]] : carry_in;
   if (t == 0) {
+    const int last = j.lastacc[f];   // position of the nearest chain before that kept samples (-1: none)
+    s_state = (last < 0 && carry_in < 0) ? 0 : min(f - last, kFar);
+    s_last = last;
+    s_from = f;
     s_count = 0;
-    s_stop = 0;
+    s_end = -1;
+    s_scanned = 0;
   }
-  int i = f, scanned = 0;   // i: position in the joint (the serial warp's)
-  for (int c0 = f; c0 < j.p; c0 += kChunk) {
-    const int n = min(kChunk, j.p - c0);
+  __syncthreads();
+  unsigned long long scanned = 0;
+  for (;;) {
+    // a pass over positions [a, p) from state st0, each thread a range
+    const int a = s_from, st0 = s_state;
+    if (a >= j.p || s_end >= 0) break;
+    const int len = j.p - a, per = (len + nt - 1) / nt;
+    const int lo = min(j.p, a + t * per), hi = min(j.p, lo + per);
+    Trans agg = tr_identity();
+    for (int q = lo; q < hi; ++q) agg = tr_then(agg, tr_position(cand_codes(j, q)));
+    s_tr[t] = agg;
+    if (t == 0) s_first = j.p;
     __syncthreads();
-    if (s_stop) break;
-    for (int q = t; q < n; q += nt) {
-      const int c = j.perm[c0 + q];
-      const int64_t kc = j.k[c];
-      s_ch[q] = c;
-      s_xu[q] = j.xused[c];
-      s_ks[q] = kc > 0 ? 1 : (kc == 0 ? 0 : -1);
-      s_m[q] = j.m[c];
+    for (int off = 1; off < nt; off <<= 1) {   // inclusive prefix of the ranges' compositions
+      const Trans prev = t >= off ? s_tr[t - off] : tr_identity();
+      __syncthreads();
+      s_tr[t] = tr_then(prev, s_tr[t]);
+      __syncthreads();
     }
-    for (int q = t; q < n * kScanCand; q += nt) s_cand[q] = cand[static_cast<size_t>(c0) * kScanCand + q];
-    __syncthreads();
-    if (t >= 32) continue;
-    bool stopped = false;
-    for (int q = 0; q < n; ++q) {
-      i = c0 + q;
-      const int ch = s_ch[q];
-      const bool known = (x == s_xu[q] && s_ks[q] >= 0);
-      bool acc;
-      if (known) {
-        acc = s_ks[q] > 0;
-      } else if (x < 0) {
-        acc = true;  // no input yet: the chain is kept whole (k = 1)
-      } else if (i - last <= kScanCand && s_cand[q * kScanCand + (i - last - 1)] < 3) {
-        const int code = s_cand[q * kScanCand + (i - last - 1)];   // the input came from i - last positions back
-        if (code == 2) {
-          stopped = true;
-          break;
-        }
-        acc = code == 1;
-        ++scanned;
-      } else {
-        const int code = scan_decide(j, i, x);   // an input from further back
-        if (code == 2) {
-          stopped = true;
-          break;
-        }
-        acc = code == 1;
-        ++scanned;
+    const int s_in = tr_at(t > 0 ? s_tr[t - 1] : tr_identity(), st0);   // state entering this range
+    // the first position entered in state kFar or kStop ends the pass
+    int s = s_in;
+    for (int q = lo; q < hi; ++q) {
+      if (s >= kFar) {
+        atomicMin(&s_first, q);
+        break;
       }
-      if (!known) {
-        if (t == 0) {
-          j.xused[ch] = x;
-          if (x < 0) {
-            j.k[ch] = 1;
-          } else if (acc) {
-            j.k[ch] = -1;
-            j.work[s_count++] = ch;
+      s = tr_at(tr_position(cand_codes(j, q)), s);
+    }
+    __syncthreads();
+    const int stop_at = s_first;
+    // the positions before it: inputs and outcomes, in parallel
+    s = s_in;
+    for (int q = lo; q < min(hi, stop_at); ++q) {
+      const unsigned long long codes = cand_codes(j, q);
+      const int ch = j.perm[q];
+      if (s == 0) {   // no input yet: the chain is kept whole
+        j.xused[ch] = -1;
+        j.k[ch] = 1;
+      } else {
+        const int c = static_cast<int>((codes >> (8 * (s - 1))) & 0xFFu);
+        if (c < 4) {   // not known for this input
+          const int src = q - s;
+          j.xused[ch] = src >= 0 ? j.m[j.perm[src]] : carry_in;
+          if (c == 1) {
+            j.k[ch] = -1;   // to be searched under the exact input
+            j.kmin[ch] = kNoHit;
+            j.work[atomicAdd(&s_count, 1)] = ch;
           } else {
             j.k[ch] = 0;
           }
+          ++scanned;
         }
-        if (acc && x >= 0 && t == 0) j.kmin[ch] = kNoHit;
       }
-      if (acc) {
-        x = s_m[q];
-        last = i;
+      s = tr_at(tr_position(codes), s);
+    }
+    if (stop_at >= j.p) break;   // uniform: every position is settled
+    // at stop_at: kStop ends the scan; kFar (the input is the last level of
+    // a chain more than kScanCand positions back) is carried one chain at a
+    // time, by one warp, until a chain keeps samples
+    if (t < 32) {
+      const int owner = (stop_at - a) / per;   // the thread whose range holds stop_at
+      int sst = tr_at(owner > 0 ? s_tr[owner - 1] : tr_identity(), st0);
+      for (int q = a + owner * per; q < stop_at; ++q) sst = tr_at(tr_position(cand_codes(j, q)), sst);
+      int end = -1, next_from = j.p;
+      if (sst == kStop) {
+        end = stop_at;
+      } else {
+        // the chain that kept samples last: kScanCand + 1 positions back if
+        // the state became kFar in this pass, else the pass's own start
+        const int last = stop_at > a ? stop_at - kFar : s_last;
+        const int x = last >= 0 ? j.m[j.perm[last]] : carry_in;
+        for (int q = stop_at; q < j.p; ++q) {
+          const int ch = j.perm[q];
+          const int64_t kc = j.k[ch];
+          const int code = (kc >= 0 && j.xused[ch] == x) ? (kc > 0 ? 5 : 4) : scan_decide(j, q, x);
+          if (code == 2) {
+            end = q;
+            break;
+          }
+          if (t == 0 && code < 4) {
+            j.xused[ch] = x;
+            ++scanned;
+            if (code == 1) {
+              j.k[ch] = -1;
+              j.kmin[ch] = kNoHit;
+              j.work[atomicAdd(&s_count, 1)] = ch;
+            } else {
+              j.k[ch] = 0;
+            }
+          }
+          if (code == 1 || code == 5) {
+            next_from = q + 1;
+            break;
+          }
+        }
+      }
+      if (t == 0) {
+        s_end = end;
+        s_from = next_from;
+        s_state = 1;
+        s_last = next_from - 1;
       }
     }
-    if (stopped) {
-      if (t == 0) s_stop = 1;
-    } else {
-      i = c0 + n;
-    }
+    __syncthreads();
   }
+  atomicAdd(&s_scanned, scanned);
   __syncthreads();
   // stopped early: chains still waiting for a search keep their inputs
   if (t == 0) {
-    for (int q = i; q < j.p; ++q)
+    for (int q = s_end >= 0 ? s_end : j.p; q < j.p; ++q)
       if (j.k[j.perm[q]] < 0) j.work[s_count++] = j.perm[q];
     j.stats[kStatPending] = s_count;
-    j.stats[kStatScanned] = scanned;
+    j.stats[kStatScanned] = static_cast<long long>(s_scanned);
   }
 }
 

@@ -102,7 +102,7 @@ def test_weight_iterations_bit_exact(L, p, S, iters, start):
                                          (128, 6, 1, 2)])
 def test_weight_iterations_bit_exact_record_and_replay(L, p, S, iters, record):
     # the joint reading the round's record of levels, and replaying every
-    # sample from the checkpoints (the default depends on L)
+    # sample from the checkpoints (the default records rounds this small)
     _run_parity(L, p, S, iters, 1, seed=2000 + L, weights=random_weights(L, L + 3, 6.0), record=record)
 
 
@@ -166,6 +166,22 @@ def test_every_resolution_path_gives_the_serial_rule(policy, L, p, S, record):
     assert mism > 0
 
 
+@pytest.mark.parametrize("record", [True, False])
+@pytest.mark.parametrize("L,p,S,scale", [(8, 300, 2, 40.0), (16, 200, 1, 30.0)])
+def test_exact_scan_long_runs_of_rejecting_chains(L, p, S, scale, record):
+    # straight to the summary and the exact scan, with weights so rough that
+    # most chains keep nothing: inputs then come from many positions back
+    # (beyond the scan's precomputed candidates), and the scan carries them
+    W = random_weights(L, seed=L + 40, scale=scale)
+    g, o, mism = _run_parity(L, p, S, 3, 1, seed=700 + L, weights=W, policy=(-1, 0, 0), record=record)
+    assert mism > 0
+    run = best = 0
+    for k in g.k:   # joint order is index order here
+        run = run + 1 if k == 0 else 0
+        best = max(best, run)
+    assert best > 8, best      # a run of rejecting chains longer than the candidate window
+
+
 @pytest.mark.parametrize("L,p,S,seg,K,C", [
     (8, 40, 200, 64 * 3, 67, 3),     # multi-sweep segments, many of them
     (8, 40, 200, 1, 200, 1),         # one sweep each
@@ -193,7 +209,7 @@ def test_segment_lengths_with_the_replay_joint(L, p, S, seg):
 
 
 def test_round_record_limit_and_memory():
-    L, p, S = 96, 5, 2            # above L = 64 rounds are recorded by default
+    L, p, S = 96, 5, 2            # rounds this small are recorded by default
     g = mc.Job(L, p, 3, 1)
     g.run_sweeps(S)
     g.join()
