@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from paper_0812_2964_gb300.workloads import WORKLOADS  # noqa: E402
+from paper_0812_2964_gb300.workloads import WORKLOADS, workload as workload_by_name  # noqa: E402
 
 METRIC = "joined-chain spin-flip attempts/s"
 UNIT = "attempts/s"
@@ -381,7 +381,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     mc.build()
-    w = WORKLOADS[args.workload]
+    w = workload_by_name(args.workload)
     S = args.sweeps or w.sweeps
     p, N = w.chains, w.N
     M = S * N
@@ -395,6 +395,8 @@ def run_gpu(args):
         job.autotune(probe_sweeps=max(1, min(S, 4_000_000 // N)))
     if args.segment_samples:
         job.set_segment_samples(args.segment_samples)
+    if args.shape:
+        job.set_launch_shape(*(int(v) for v in args.shape.split(",")))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
 
     with torch.cuda.stream(stream):
@@ -648,7 +650,10 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", default=WORKLOAD,
-                    help="L32_p16384 (default), L64_p4096, L128_p1024, L8_p64, batch_uneven, serving or fig2")
+                    help="L32_p16384 (default), L64_p4096, L128_p1024, L8_p64, batch_uneven, serving, fig2, "
+                         "or L<L>_p<chains> (one job of that size, 20 sweeps a round)")
+    ap.add_argument("--shape", default="", help="launch shape placement,chains_per_warp,warps_per_block "
+                                                "(0 registers, 1 shared memory, 2 global memory)")
     ap.add_argument("--sweeps", type=int, default=0, help="override sweeps per iteration")
     ap.add_argument("--tune", action="store_true", help="pick the launch shape with mc_autotune first")
     ap.add_argument("--segment-samples", type=int, default=0,

@@ -48,6 +48,19 @@ WORKLOADS = {
     "L20_p32": Workload("L20_p32", 20, 32, 1, 10, 10, 1, "Fig. 2 lattice"),
 }
 
+
+def workload(name: str) -> Workload:
+    """A named workload, or an ad-hoc one named L<L>_p<chains> (20 sweeps a
+    round, seed 11, random start) -- the size of one served job."""
+    if name in WORKLOADS:
+        return WORKLOADS[name]
+    import re
+    m = re.fullmatch(r"L(\d+)_p(\d+)", name)
+    if not m:
+        raise KeyError(f"unknown workload {name!r}")
+    return Workload(name, int(m.group(1)), int(m.group(2)), 20, 10, 11, 1, "ad hoc")
+
+
 # uneven sizes in one batch
 BATCH_GROUPS = [(16, 8192, 4), (24, 4096, 5), (32, 4096, 6), (48, 2048, 7), (64, 1024, 8)]
 
