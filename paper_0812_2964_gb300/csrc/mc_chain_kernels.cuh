@@ -439,7 +439,8 @@ __device__ __forceinline__ void record_segment(const DevJob& j, int i, int seg, 
 template <class Factory, bool TSMEM>
 __global__ void __launch_bounds__(128) search_kernel(const DevJob j, const int cpw, const uint64_t t0,
                                                      const int64_t S, const uint32_t r, const int list_mode,
-                                                     const int seg_lo, const int seg_hi_in) {
+                                                     const int seg_lo, const int seg_hi_in, const int exact_first) {
+  if (exact_first && rough_last_joint(j.stats[kStatRejected], j.p)) return;   // (the first search only)
   const int nchains = list_mode == 0 ? j.p : static_cast<int>(j.stats[list_mode == 1 ? kStatPending : kStatNoHit]);
   const int seg_hi = min(seg_hi_in, j.ck_K);
   const long long items = static_cast<long long>(nchains) * max(0, seg_hi - seg_lo);
@@ -846,33 +847,35 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
       std::min<long long>(blocks_for(items, per_block), resident_blocks(kq, 32 * s.wpb, bytes)));
   // a search over the chains of list_mode: their first segments, then the
   // later segments of those without a hit there
-  auto search = [&](int list_mode) -> cudaError_t {
+  const bool exact_scan = static_cast<long long>(j.p) * S * j.N <= j.scan_max_samples;
+  // a recorded round may skip the speculative first search (rough_last_joint)
+  const int exact_first = (IsRec<F>::value && exact_scan) ? 1 : 0;
+  auto search = [&](int list_mode, int first) -> cudaError_t {
     cudaError_t e2 = join_reset_queue(j, st);
     if (e2 != cudaSuccess) return e2;
-    kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, list_mode, 0, 1);
+    kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, list_mode, 0, 1, first);
     launches_add(1);
     if (j.ck_K > 1) {
       if ((e2 = join_nohit(j, list_mode, st)) != cudaSuccess) return e2;
       if ((e2 = join_reset_queue(j, st)) != cudaSuccess) return e2;
-      kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, 2, 1, j.ck_K);
+      kq<<<grid_all, 32 * s.wpb, bytes, st>>>(j, s.cpw, t0, S, r, 2, 1, j.ck_K, first);
       launches_add(1);
     }
     return cudaGetLastError();
   };
   // speculated inputs: every chain
-  if ((e = search(0)) != cudaSuccess) return e;
-  if ((e = join_select(j, false, st)) != cudaSuccess) return e;
+  if ((e = search(0, exact_first)) != cudaSuccess) return e;
+  if ((e = join_select(j, false, st, exact_first != 0)) != cudaSuccess) return e;
   // grid-wide speculative resolution passes
   auto pass = [&](int n, bool defer) -> cudaError_t {
     for (int q = 0; q < n; ++q) {
       cudaError_t e2 = join_mark(j, st, true, defer);
-      if (e2 == cudaSuccess) e2 = search(1);
+      if (e2 == cudaSuccess) e2 = search(1, 0);
       if (e2 == cudaSuccess) e2 = join_select(j, true, st);
       if (e2 != cudaSuccess) return e2;
     }
     return cudaSuccess;
   };
-  const bool exact_scan = static_cast<long long>(j.p) * S * j.N <= j.scan_max_samples;
   if (exact_scan) {
     // a few speculative passes; if chains are still pending, the summary
     // replay and the exact scan settle every input, one search finds the
@@ -891,7 +894,7 @@ inline cudaError_t launch_join_t(const DevJob& j, const LaunchShape& s, uint64_t
     launches_add(1);
     if ((e = join_scan(j, st)) != cudaSuccess) return e;
     if ((e = join_tj_list(j, st)) != cudaSuccess) return e;
-    if ((e = search(1)) != cudaSuccess) return e;
+    if ((e = search(1, 0)) != cudaSuccess) return e;
     if ((e = join_select(j, true, st)) != cudaSuccess) return e;
     if ((e = pass(j.passes_scan, false)) != cudaSuccess) return e;
   } else {

@@ -104,6 +104,13 @@ constexpr long long kPartialLevelsMax = 1ll << 26;
 // kmin[] value of a chain with no accepted sample found (yet)
 constexpr unsigned long long kNoHit = 0x7FFFFFFFFFFFFFFFull;
 
+// Whether the job's previous joint rejected so many chains that this one
+// skips its speculative first search (where the caller allows it): with more
+// than p/16 of them, the speculated inputs fail for as many chains and the
+// joint takes the exact path anyway, and the speculative search would have
+// read every rejecting chain whole
+__host__ __device__ inline bool rough_last_joint(long long rejected, int p) { return rejected > p / 16; }
+
 enum StatIndex : int {
   kStatCarry = 0,        // level passed on to the next round's chain 0
   kStatCarryValid = 1,
@@ -158,7 +165,11 @@ cudaError_t join_mark(const DevJob& j, cudaStream_t st, bool thresholds = true, 
 cudaError_t join_tj_list(const DevJob& j, cudaStream_t st);
 // list (in work2) the chains of list_mode (0 all, 1 work) with no hit in segment 0
 cudaError_t join_nohit(const DevJob& j, int list_mode, cudaStream_t st);
-cudaError_t join_select(const DevJob& j, bool listed, cudaStream_t st);
+// exact_first: a recorded round whose exact path is enabled -- when the job's
+// previous joint rejected more than p/16 chains, the speculative first
+// search is skipped (select marks every chain unsearched) and the joint goes
+// straight to the summary and the exact scan
+cudaError_t join_select(const DevJob& j, bool listed, cudaStream_t st, bool exact_first = false);
 cudaError_t join_prefix_list(const DevJob& j, cudaStream_t st);
 cudaError_t join_reset_queue(const DevJob& j, cudaStream_t st);
 cudaError_t join_finalize(const DevJob& j, int64_t S, cudaStream_t st);

@@ -993,11 +993,15 @@ cudaError_t join_prelude(const DevJob& j, cudaStream_t st) {
 }
 
 // k_i = the earliest accepted sample the search found (0: none).
-__global__ void select_kernel(const DevJob j, const int listed) {
+__global__ void select_kernel(const DevJob j, const int listed, const int exact_first) {
   const int n = listed ? static_cast<int>(j.stats[kStatPending]) : j.p;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const int i = listed ? j.work[q] : q;
+  if (exact_first && rough_last_joint(j.stats[kStatRejected], j.p)) {
+    j.k[i] = -1;   // not searched: every chain waits for the exact path
+    return;
+  }
   const unsigned long long k = j.kmin[i];
   j.k[i] = k == kNoHit ? 0 : static_cast<int64_t>(k);
 }
@@ -1072,8 +1076,8 @@ cudaError_t join_prefix_list(const DevJob& j, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t join_select(const DevJob& j, bool listed, cudaStream_t st) {
-  select_kernel<<<blocks_for(j.p, 256), 256, 0, st>>>(j, listed ? 1 : 0);
+cudaError_t join_select(const DevJob& j, bool listed, cudaStream_t st, bool exact_first) {
+  select_kernel<<<blocks_for(j.p, 256), 256, 0, st>>>(j, listed ? 1 : 0, !listed && exact_first ? 1 : 0);
   launches_add(1);
   return cudaGetLastError();
 }
