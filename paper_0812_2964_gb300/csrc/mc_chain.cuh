@@ -350,19 +350,26 @@ __device__ __forceinline__ void joint_fill(uint32_t (&U)[32], const int nb, cons
 // poll() (once per sweep) ends the search early when another search has
 // already found an accepted sample of the same chain at or before `stop`
 // (the chain's earliest hit so far, *kmin; nullptr: never).
+// (k counts the samples of the words seen so far; sample b of the current
+// word is kw + b + 1, with no per-sample counter.)
 struct SearchHook {
   const uint32_t* __restrict__ tj;  // thresholds for moves x -> m, indexed by m
   int64_t k, M, found;
+  int64_t kw = 0;                   // samples before the current word
   uint32_t chain, r, k0, k1;
   uint32_t uj[32];
   bool done;
   const unsigned long long* kmin = nullptr;
   unsigned long long stop = 0;
-  __device__ __forceinline__ void word(int nb) { joint_fill(uj, nb, k, r, chain, k0, k1); }
+  __device__ __forceinline__ void word(int nb) {
+    joint_fill(uj, nb, k, r, chain, k0, k1);
+    kw = k;
+    k += nb;
+  }
   __device__ __forceinline__ void sample(int m4, int b) {
-    ++k;
-    const bool hit = (uj[b] <= __ldg(&tj[m4 >> 2])) && !done && k <= M;
-    found = hit ? k : found;
+    const int64_t kk = kw + b + 1;
+    const bool hit = (uj[b] <= __ldg(&tj[m4 >> 2])) && !done && kk <= M;
+    found = hit ? kk : found;
     done = done || hit;
   }
   __device__ __forceinline__ void poll() {
@@ -422,10 +429,12 @@ struct SummaryHook {
     }
   }
   __device__ __forceinline__ void poll() {}
-  __device__ __forceinline__ void word(int nb) { joint_fill(uj, nb, k, r, chain, k0, k1); }
+  __device__ __forceinline__ void word(int nb) {
+    joint_fill(uj, nb, k, r, chain, k0, k1);
+    k += nb;
+  }
   __device__ __forceinline__ void sample(int m4, int b) {
     const int m = m4 >> 2;
-    ++k;
     const uint32_t u = uj[b];
     if (m != cur) {
       flush();

@@ -559,20 +559,21 @@ __global__ void __launch_bounds__(128) summary_kernel(const DevJob j, const int 
     atomicAdd(reinterpret_cast<unsigned long long*>(&j.stats[kStatSearched]), static_cast<unsigned long long>(searched));
 }
 
+// (k counts the samples of the words seen so far, as in SearchHook; done
+// once a word reaches the cut)
 struct PrefixHook {
   uint32_t* hist;
   int64_t k, cut;  // samples with index < cut are counted
   bool done;
+  int64_t kw = 0;
   __device__ __forceinline__ void poll() {}
-  __device__ __forceinline__ void word(int) {}
-  __device__ __forceinline__ void sample(int m4, int) {
-    if (done) return;
-    ++k;
-    if (k >= cut) {
-      done = true;
-      return;
-    }
-    red_shared_add(hist, m4, 1u);
+  __device__ __forceinline__ void word(int nb) {
+    kw = k;
+    k += nb;
+    done = done || k >= cut;
+  }
+  __device__ __forceinline__ void sample(int m4, int b) {
+    if (kw + b + 1 < cut) red_shared_add(hist, m4, 1u);
   }
 };
 
