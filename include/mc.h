@@ -136,11 +136,14 @@ int mc_set_partial_record(mc_job *job, int64_t max_entries);
  * (chain 0: by the previous round; in the job's first round chain 0 is kept
  * whole); a chain with no such sample keeps nothing and passes on what it
  * received.  Kept samples are added to h.  The serial rule is evaluated in
- * parallel: speculative searches from lattice checkpoints, resolution
- * passes, an exact scan over per-level summaries when speculation does not
- * settle; the result is that of the serial rule.  Asynchronous; if
- * joined_len is not NULL the call synchronises and stores the number of
- * samples kept in this round.  MC_ESTATE without a pending round. */
+ * parallel: speculative searches over the round's samples (read from its
+ * record, or replayed from lattice checkpoints), resolution passes, an exact
+ * scan over per-level summaries when speculation does not settle (a
+ * recorded round goes straight to it when the job's previous joint rejected
+ * more than p/16 chains); the result is that of the serial rule.
+ * Asynchronous; if joined_len is not NULL the call synchronises and stores
+ * the number of samples kept in this round.  MC_ESTATE without a pending
+ * round. */
 int mc_join(mc_job *job, int64_t *joined_len);
 
 /* The control of Sec. 5 / Fig. 2: concatenate the last round's chains whole,
