@@ -108,6 +108,21 @@ __device__ __forceinline__ void red_shared_add(uint32_t* base, const int byte_of
 #endif
 }
 
+// 8-byte global store of the round record, opaque to the compiler's memory
+// ordering (no memory clobber): nothing in the sweep reads the record, and
+// a plain store held back the threshold loads scheduled around it.
+// (A host compiler gets a plain store.)
+__device__ __forceinline__ void st_record(uint16_t* p, uint32_t a, uint32_t b) {
+#ifdef __CUDACC__
+  asm volatile("st.global.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(a), "r"(b));
+#else
+  p[0] = static_cast<uint16_t>(a);
+  p[1] = static_cast<uint16_t>(a >> 16);
+  p[2] = static_cast<uint16_t>(b);
+  p[3] = static_cast<uint16_t>(b >> 16);
+#endif
+}
+
 // Byte permute (PTX prmt, generic mode): selector nibble bit 3 set means
 // "replicate the sign of the selected byte".
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t sel) {
@@ -285,14 +300,14 @@ struct GenHook {
   int pend[D];       // byte offsets (4 m) of the samples not counted yet
   uint16_t* rec;     // REC: the chain's next record entry (always a valid address)
   bool rec_on;       // REC: this lane writes the record (one lane per chain)
-  uint32_t pk0, pk1; // REC: levels of the current group of four samples
+  uint32_t pk[2];    // REC: levels of the current group of four samples
   __device__ __forceinline__ void init(uint32_t* h, uint32_t i, int np1) {
     hist = h;
     inc = i;
     scratch = 4 * np1;
     rec = nullptr;
     rec_on = false;
-    pk0 = pk1 = 0u;
+    pk[0] = pk[1] = 0u;
 #pragma unroll
     for (int b = 0; b < D; ++b) pend[b] = scratch;
   }
@@ -302,14 +317,12 @@ struct GenHook {
     pend[b % D] = m4;
     if constexpr (REC) {
       const uint32_t lv = static_cast<uint32_t>(m4) >> 2;
-      switch (b & 3) {
-        case 0: pk0 = lv; break;
-        case 1: pk0 |= lv << 16; break;
-        case 2: pk1 = lv; break;
-        default:
-          pk1 |= lv << 16;
-          if (rec_on) *reinterpret_cast<uint2*>(rec) = make_uint2(pk0, pk1);
-          rec += kRecGroupStride;
+      const int q = (b & 3) >> 1;   // (b is a compile-time constant: static indices)
+      if (b & 1) pk[q] |= lv << 16;
+      else pk[q] = lv;
+      if ((b & 3) == 3) {
+        if (rec_on) st_record(rec, pk[0], pk[1]);
+        rec += kRecGroupStride;
       }
     }
   }
