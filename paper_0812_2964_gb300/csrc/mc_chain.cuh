@@ -214,7 +214,7 @@ __device__ __forceinline__ void sweep_row(uint32_t (&cur)[WD], const uint32_t (&
     {
       // first site of the word: state before it is known, one load
       const int a4 = static_cast<int>(prmt(A0[0], 0x4440u)) + static_cast<int>(f) * static_cast<int>(prmt(D[0], 0x8880u));
-      t0 = t1 = *reinterpret_cast<const uint32_t*>(Tb + a4 * np1 + m4);
+      t0 = t1 = *reinterpret_cast<const uint32_t*>(Tb + (a4 * np1 + m4));
     }
 #pragma unroll
     for (int b = 0; b < 32; ++b) {
@@ -248,9 +248,11 @@ __device__ __forceinline__ void sweep_row(uint32_t (&cur)[WD], const uint32_t (&
             na0 = static_cast<int>(prmt(A0[(b + 1) >> 2], 0x4440u | static_cast<uint32_t>((b + 1) & 3)));
             nd4 = static_cast<int>(prmt(D[(b + 1) >> 2], sign_sel(static_cast<uint32_t>((b + 1) & 3))));
           }
+          // (offsets summed as 32-bit integers, one 64-bit address add each)
           const int off0 = na0 * np1 + m4;                 // site b not flipped
+          const int off1 = off0 + nd4 * np1 + dl;          // site b flipped
           t0 = *reinterpret_cast<const uint32_t*>(Tb + off0);
-          t1 = *reinterpret_cast<const uint32_t*>(Tb + off0 + nd4 * np1 + dl);   // site b flipped
+          t1 = *reinterpret_cast<const uint32_t*>(Tb + off1);
         }
         if (acc) {   // (predicated: no multiply by the 0/1 outcome)
           F |= 1u << b;
