@@ -397,6 +397,8 @@ def run_gpu(args):
         job.set_segment_samples(args.segment_samples)
     if args.shape:
         job.set_launch_shape(*(int(v) for v in args.shape.split(",")))
+    if args.round_record >= 0:
+        job.set_round_record(args.round_record)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
 
     with torch.cuda.stream(stream):
@@ -654,6 +656,10 @@ def main(argv=None):
                          "or L<L>_p<chains> (one job of that size, 20 sweeps a round)")
     ap.add_argument("--shape", default="", help="launch shape placement,chains_per_warp,warps_per_block "
                                                 "(0 registers, 1 shared memory, 2 global memory)")
+    ap.add_argument("--round-record", type=int, default=-1,
+                    help="largest round (samples) whose levels are recorded for the joint (0: none; "
+                         "default: the library's); a short profiling run of the headline kernel uses 0, "
+                         "as the full-size round is too large to record")
     ap.add_argument("--sweeps", type=int, default=0, help="override sweeps per iteration")
     ap.add_argument("--tune", action="store_true", help="pick the launch shape with mc_autotune first")
     ap.add_argument("--segment-samples", type=int, default=0,

@@ -28,7 +28,7 @@ __all__ = ["build", "McError", "mc_info", "Job", "lib", "mc_kernel_launches"] + 
     "mc_server_get_info", "mc_server_clock", "mc_server_free", "Server"]
 
 # revision of the generation kernel; bump when it changes (profiles record it)
-KERNEL_REV = "gen-5"
+KERNEL_REV = "gen-6"
 
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ESTATE, MC_ETIMEOUT = 0, -1, -2, -3, -4, -5
 _NAMES = {MC_EINVAL: "MC_EINVAL", MC_ENOMEM: "MC_ENOMEM", MC_ECUDA: "MC_ECUDA",
