@@ -7,6 +7,7 @@ import subprocess
 import sys
 
 import numpy as np
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -41,3 +42,15 @@ def test_serving_stream_shape():
     mean_attempts = np.mean([j.chains * j.L ** 2 * j.sweeps * j.iterations for j in s])
     assert 8e9 < mean_attempts < 12e9                        # about 9.7e9 attempts per job
     assert serving_stream(50) == serving_stream(2000)[:50]   # the same seeded stream
+
+
+def test_workload_names():
+    # named workloads, and one job of any size as L<L>_p<chains> (the size of a served job)
+    sys.path.insert(0, ROOT)
+    from paper_0812_2964_gb300.workloads import WORKLOADS, workload
+
+    assert workload("L32_p16384") is WORKLOADS["L32_p16384"]
+    w = workload("L96_p2048")
+    assert (w.L, w.chains, w.sweeps, w.N) == (96, 2048, 20, 96 * 96)
+    with pytest.raises(KeyError):
+        workload("L96")
