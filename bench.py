@@ -239,7 +239,7 @@ def alu_roofline(p, S, N, gen_ms):
 # reduced sizes of the other workloads measured beside the headline (one line)
 SUB = dict(L64_sweeps=2000, L128_sweeps=400, job_steps=3, job_warmup=3,
            batch_sweeps=5000, batch_steps=2, batch_warmup=1,
-           serving_jobs=60, serving_rate=20.0, serving_sweeps=20, serving_slots=64)
+           serving_jobs=60, serving_rate=20.0, serving_sweeps=20, serving_slots=16)
 
 
 def job_record(torch, mc, device, workload, S, steps, warmup):
@@ -671,7 +671,9 @@ def main(argv=None):
                     help="skip the reduced-size L=64, L=128, batch and serving records of the default run")
     ap.add_argument("--jobs", type=int, default=400, help="serving: jobs in the arrival stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
-    ap.add_argument("--slots", type=int, default=64, help="serving: server slots")
+    ap.add_argument("--slots", type=int, default=16,
+                    help="serving: server slots (16 hold the GPU's capacity; more resident jobs only "
+                         "lengthen each job)")
     ap.add_argument("--join-order", type=int, default=0,
                     help="0: chains joined in index order; 1: by ascending final energy (end of Sec. 2)")
     ap.add_argument("--mtotal", type=int, default=100_000_000, help="fig2: samples per weight iteration (M_total)")
