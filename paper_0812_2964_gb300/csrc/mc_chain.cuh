@@ -451,7 +451,27 @@ struct SummaryHook {
   __device__ __forceinline__ void sample(int m4, int b) {
     const int m = m4 >> 2;
     const uint32_t u = uj[b];
-    if (m != cur) {
+    if constexpr (W > 0) {
+      // (branch-light: the range and the flag are kept per sample, the run
+      // that ends here is one short conditional update of the window; only a
+      // level outside the window takes the atomic)
+      const bool put_run = m != cur && cur >= 0;
+      base = (base == kNoBase) ? m - W / 2 : base;
+      const unsigned s = static_cast<unsigned>(cur - base);
+      if (put_run) {
+        if (s < static_cast<unsigned>(W)) {
+          uint32_t* e = win + s * kWinStride;
+          *e = min(*e, run_min);
+        } else {
+          atomicMin(&umin[cur], run_min);
+        }
+      }
+      flag = flag || (put_run && run_min == 0xFFFFFFFFu);
+      lo = min(lo, m);
+      hi = max(hi, m);
+      run_min = (m != cur) ? u : min(run_min, u);
+      cur = m;
+    } else if (m != cur) {
       flush();
       cur = m;
       run_min = u;
