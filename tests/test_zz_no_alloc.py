@@ -13,8 +13,11 @@ pytestmark = pytest.mark.gpu
 
 
 # L = 100 and 128 read the threshold table straight from the fixed scratch
-# (it does not fit in shared memory); 128 fills the whole scratch
-@pytest.mark.parametrize("L,p,S", [(32, 300, 3), (48, 40, 2), (8, 70, 5), (100, 8, 1), (128, 8, 1)])
+# (it does not fit in shared memory); 128 fills the whole scratch.  L = 96,
+# and L = 128 with more than 8 chains a warp (4900 chains over 608 warps),
+# sweep their lattices in place in the caller's spin buffer.
+@pytest.mark.parametrize("L,p,S", [(32, 300, 3), (48, 40, 2), (8, 70, 5), (100, 8, 1), (128, 8, 1),
+                                   (96, 40, 1), (128, 4900, 1)])
 def test_noalloc_generation_matches_job_api(L, p, S):
     torch = pytest.importorskip("torch")
     mc.build()
