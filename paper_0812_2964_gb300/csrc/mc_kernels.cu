@@ -7,6 +7,7 @@
 #include <math_constants.h>
 
 #include "mc_chain_kernels.cuh"
+#include "mc_scan_fsm.cuh"
 
 namespace mcgpu {
 
@@ -433,8 +434,7 @@ __global__ void summary_init_kernel(const DevJob j) {
 // current input came from -- whose per-position transition functions are
 // composed by a block-wide prefix scan, so the scan costs O(p / 1024) and
 // not O(p); only an input from further back than kScanCand positions is
-// evaluated one chain at a time.
-constexpr int kScanCand = 8;
+// evaluated one chain at a time.  The state machine is in mc_scan_fsm.cuh.
 
 __device__ __forceinline__ uint8_t* scan_cand(const DevJob& j) {
   return reinterpret_cast<uint8_t*>(j.summ + 3 * static_cast<size_t>(j.p));   // [p][kScanCand]
@@ -461,12 +461,11 @@ __device__ __forceinline__ int scan_decide(const DevJob& j, int pos, int x) {
   }
   hit = __any_sync(0xFFFFFFFFu, hit);
   amb = __any_sync(0xFFFFFFFFu, amb);
-  return hit ? 1 : (amb ? 2 : 0);
+  return hit ? kAnsYes : (amb ? kAnsUndecided : kAnsNo);
 }
 
-// Answer codes: 0 keeps nothing, 1 keeps samples, 2 undecidable (the scan
-// stops there), 3 no such input, 4 / 5 as 0 / 1 but k is already known for
-// this input (nothing to write).
+// The answer codes of chain q under the inputs of the kScanCand positions
+// before it (mc_scan_fsm.cuh).
 __global__ void __launch_bounds__(256) cand_kernel(const DevJob j) {
   if (j.stats[kStatPending] == 0) return;
   const int f = static_cast<int>(j.stats[kStatFirstPending]);
@@ -479,51 +478,14 @@ __global__ void __launch_bounds__(256) cand_kernel(const DevJob j) {
     const int q = f + static_cast<int>(w / kScanCand), d = 1 + static_cast<int>(w % kScanCand);
     const int src = q - d;
     const int x = src >= 0 ? j.m[j.perm[src]] : (src == -1 ? carry_in : -1);
-    int code = 3;
+    int code = kAnsNone;
     if (x >= 0) {
       const int ch = j.perm[q];
       const int64_t kc = j.k[ch];
-      code = (kc >= 0 && j.xused[ch] == x) ? (kc > 0 ? 5 : 4) : scan_decide(j, q, x);
+      code = (kc >= 0 && j.xused[ch] == x) ? (kc > 0 ? kAnsKnownYes : kAnsKnownNo) : scan_decide(j, q, x);
     }
     if (lane == 0) cand[static_cast<size_t>(q) * kScanCand + d - 1] = static_cast<uint8_t>(code);
   }
-}
-
-// Scan states: 0 no input yet (the chain is kept whole), d = 1..8 the input
-// is the last level of the chain d positions back, kFar from further back,
-// kStop undecidable.  A transition function holds the next state of every
-// state in 4-bit fields.
-constexpr int kFar = 9, kStop = 10, kStates = 11;
-using Trans = unsigned long long;
-
-__device__ __forceinline__ int tr_at(Trans T, int s) { return static_cast<int>((T >> (4 * s)) & 15u); }
-
-__device__ __forceinline__ Trans tr_identity() {
-  Trans r = 0;
-#pragma unroll
-  for (int s = 0; s < kStates; ++s) r |= static_cast<Trans>(s) << (4 * s);
-  return r;
-}
-
-// B after A
-__device__ __forceinline__ Trans tr_then(Trans A, Trans B) {
-  Trans r = 0;
-#pragma unroll
-  for (int s = 0; s < kStates; ++s) r |= static_cast<Trans>(tr_at(B, tr_at(A, s))) << (4 * s);
-  return r;
-}
-
-// the transition of a position from its answer codes (one byte per d)
-__device__ __forceinline__ Trans tr_position(unsigned long long codes) {
-  Trans r = static_cast<Trans>(1) | (static_cast<Trans>(kFar) << (4 * kFar)) |
-            (static_cast<Trans>(kStop) << (4 * kStop));
-#pragma unroll
-  for (int d = 1; d <= kScanCand; ++d) {
-    const int c = static_cast<int>((codes >> (8 * (d - 1))) & 0xFFu);
-    const int next = (c == 1 || c == 5) ? 1 : (c == 0 || c == 4) ? (d == kScanCand ? kFar : d + 1) : kStop;
-    r |= static_cast<Trans>(next) << (4 * d);
-  }
-  return r;
 }
 
 __device__ __forceinline__ unsigned long long cand_codes(const DevJob& j, int q) {
@@ -534,7 +496,6 @@ __device__ __forceinline__ unsigned long long cand_codes(const DevJob& j, int q)
 
 __global__ void __launch_bounds__(1024) scan_kernel(const DevJob j) {
   if (j.stats[kStatPending] == 0) return;
-  static_assert(kScanCand == 8 && kStates <= 16, "answer codes in one 64-bit word, states in 4 bits");
   __shared__ Trans s_tr[1024];
   __shared__ int s_first, s_count, s_state, s_from, s_last, s_end;
   __shared__ unsigned long long s_scanned;
@@ -591,10 +552,10 @@ __global__ void __launch_bounds__(1024) scan_kernel(const DevJob j) {
         j.k[ch] = 1;
       } else {
         const int c = static_cast<int>((codes >> (8 * (s - 1))) & 0xFFu);
-        if (c < 4) {   // not known for this input
+        if (c < kAnsKnownNo) {   // not known for this input
           const int src = q - s;
           j.xused[ch] = src >= 0 ? j.m[j.perm[src]] : carry_in;
-          if (c == 1) {
+          if (c == kAnsYes) {
             j.k[ch] = -1;   // to be searched under the exact input
             j.kmin[ch] = kNoHit;
             j.work[atomicAdd(&s_count, 1)] = ch;
@@ -625,15 +586,15 @@ __global__ void __launch_bounds__(1024) scan_kernel(const DevJob j) {
         for (int q = stop_at; q < j.p; ++q) {
           const int ch = j.perm[q];
           const int64_t kc = j.k[ch];
-          const int code = (kc >= 0 && j.xused[ch] == x) ? (kc > 0 ? 5 : 4) : scan_decide(j, q, x);
-          if (code == 2) {
+          const int code = (kc >= 0 && j.xused[ch] == x) ? (kc > 0 ? kAnsKnownYes : kAnsKnownNo) : scan_decide(j, q, x);
+          if (code == kAnsUndecided) {
             end = q;
             break;
           }
-          if (t == 0 && code < 4) {
+          if (t == 0 && code < kAnsKnownNo) {
             j.xused[ch] = x;
             ++scanned;
-            if (code == 1) {
+            if (code == kAnsYes) {
               j.k[ch] = -1;
               j.kmin[ch] = kNoHit;
               j.work[atomicAdd(&s_count, 1)] = ch;
@@ -641,7 +602,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const DevJob j) {
               j.k[ch] = 0;
             }
           }
-          if (code == 1 || code == 5) {
+          if (code == kAnsYes || code == kAnsKnownYes) {
             next_from = q + 1;
             break;
           }

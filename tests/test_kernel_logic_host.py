@@ -2,7 +2,8 @@
 dwell-time histogram) and the joint's replay hooks (per-word joint
 uniforms, first accepted sample, per-level minimum uniforms) compiled for
 the host and checked against the oracle for every supported lattice size,
-before any of it runs on a GPU."""
+before any of it runs on a GPU; and the joint's exact-scan state machine
+checked against the serial rule it stands for."""
 import os
 import shutil
 import subprocess
@@ -30,3 +31,19 @@ def test_sweep_row_matches_oracle_on_host(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.count(": ok") == 13
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="g++ not available")
+def test_scan_state_machine_matches_the_serial_rule_on_host(tmp_path):
+    """The exact scan's per-position transition functions (compiled for the
+    host), composed one by one and through the block scan's ranges and
+    Hillis-Steele prefix, give every position the input the serial rule of
+    Sec. 2 passes to it; kFar and kStop begin exactly where they should."""
+    exe = tmp_path / "fsm"
+    subprocess.check_call(["g++", "-O2", "-std=c++17",
+                           "-include", os.path.join(HERE, "host_emu", "cuda_stub.h"),
+                           "-I", os.path.join(ROOT, "paper_0812_2964_gb300", "csrc"),
+                           os.path.join(HERE, "host_emu", "scan_fsm_vs_serial.cpp"), "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "algebra: ok" in r.stdout and "serial rule: ok" in r.stdout, r.stdout
