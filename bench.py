@@ -645,6 +645,67 @@ def run_fig2(args):
     return 0
 
 
+def run_fig1(args):
+    """The Fig. 1 comparison (Sec. 5) at the paper's lattice size and number
+    of weight iterations: L = 100, I = 1300 iterations of the weight
+    recursion from W = 0, each one round of `sweeps` sweeps on every chain
+    joined by detailed balance; then E/N, C/N, F/N and S/N by Eq.
+    (reweighting2) against the exact finite-lattice values (Ferdinand and
+    Fisher; Kaufman's partition function).  The paper ran 32 chains of 313
+    sweeps (M_total = 1e8 a iteration); here many short chains make each
+    iteration's sample larger and its round shorter.  The loop stops early,
+    at a whole iteration, once `time_limit` seconds have passed."""
+    import torch
+
+    import paper_0812_2964_gb300 as mc
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from exact import exact_thermo
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    mc.build()
+    L = 100
+    N = L * L
+    p = args.chains or 4096
+    S = args.sweeps or 20
+    iters = args.iters or 1300
+    betas = [0.1, 0.2, 0.3, 0.4, 0.42, 0.4406867935097715, 0.46, 0.5, 0.6, 0.8, 1.0]
+    job = mc.Job(L, p, 9 + rank, 1)
+    kept = 0
+    done = 0
+    t0 = time.perf_counter()
+    while done < iters and time.perf_counter() - t0 < args.time_limit:
+        job.run_sweeps(S)
+        kept += job.join()
+        job.update_weights()
+        done += 1
+    job.sync()
+    el = time.perf_counter() - t0
+    got = job.thermo(betas)
+    visited = int(np.count_nonzero(job.visited))
+    job.close()
+    rows = []
+    for b, g in zip(betas, got):
+        ex = exact_thermo(L, b)
+        rows.append({"beta": b, "E": float(g[0]) / N, "C": float(g[1]) / N, "F": float(g[2]) / N,
+                     "S": float(g[3]) / N, "E_exact": ex[0] / N, "C_exact": ex[1] / N, "F_exact": ex[2] / N,
+                     "S_exact": ex[3] / N})
+    dev = {q: max(abs(r[q] - r[q + "_exact"]) for r in rows) for q in ("E", "C", "F", "S")}
+    line = {"metric": "fig1: largest deviation of E/N, C/N, F/N, S/N from the exact L=100 values",
+            "unit": "per site", "value": max(dev["E"], dev["F"], dev["S"]), "higher_is_better": False,
+            "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "fig1", "L": L, "chains": p, "sweeps_per_iteration": S,
+                       "samples_per_iteration": p * S * N, "iterations": done, "iterations_asked": iters,
+                       "seed": 9 + rank, "start": "random", "betas": betas},
+            "max_abs_dev": dev, "levels_visited": visited, "levels": N + 1,
+            "kept_fraction": kept / max(1, done * p * S * N), "seconds": el,
+            "ms_per_iteration": 1e3 * el / max(1, done), "rows": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -652,7 +713,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", default=WORKLOAD,
-                    help="L32_p16384 (default), L64_p4096, L128_p1024, L8_p64, batch_uneven, serving, fig2, "
+                    help="L32_p16384 (default), L64_p4096, L128_p1024, L8_p64, batch_uneven, serving, fig1, fig2, "
                          "or L<L>_p<chains> (one job of that size, 20 sweeps a round)")
     ap.add_argument("--shape", default="", help="launch shape placement,chains_per_warp,warps_per_block "
                                                 "(0 registers, 1 shared memory, 2 global memory)")
@@ -677,7 +738,10 @@ def main(argv=None):
     ap.add_argument("--join-order", type=int, default=0,
                     help="0: chains joined in index order; 1: by ascending final energy (end of Sec. 2)")
     ap.add_argument("--mtotal", type=int, default=100_000_000, help="fig2: samples per weight iteration (M_total)")
-    ap.add_argument("--iters", type=int, default=20, help="fig2: weight iterations")
+    ap.add_argument("--iters", type=int, default=0, help="fig1, fig2: weight iterations (default 1300, 20)")
+    ap.add_argument("--chains", type=int, default=0, help="fig1: chains (default 4096)")
+    ap.add_argument("--time-limit", type=float, default=600.0,
+                    help="fig1: stop after the iteration that passes this many seconds")
     ap.add_argument("--mnode", type=int, default=100, help="fig2: attempts per chain per round (M_node)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
@@ -687,7 +751,10 @@ def main(argv=None):
     if args.workload == "serving":
         return run_serving(args)
     if args.workload == "fig2":
+        args.iters = args.iters or 20
         return run_fig2(args)
+    if args.workload == "fig1":
+        return run_fig1(args)
     return run_gpu(args)
 
 
