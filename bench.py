@@ -652,9 +652,10 @@ def run_fig1(args):
     joined by detailed balance; then E/N, C/N, F/N and S/N by Eq.
     (reweighting2) against the exact finite-lattice values (Ferdinand and
     Fisher; Kaufman's partition function).  The paper ran 32 chains of 313
-    sweeps (M_total = 1e8 a iteration); here many short chains make each
-    iteration's sample larger and its round shorter.  The loop stops early,
-    at a whole iteration, once `time_limit` seconds have passed."""
+    sweeps and repeated rounds until M_total = 1e8 samples were kept before
+    each update (step 6; `--mtotal 0`: one round per iteration).  The loop
+    stops early, at a whole iteration, once `time_limit` seconds have
+    passed."""
     import torch
 
     import paper_0812_2964_gb300 as mc
@@ -672,13 +673,18 @@ def run_fig1(args):
     iters = args.iters or 1300
     betas = [0.1, 0.2, 0.3, 0.4, 0.42, 0.4406867935097715, 0.46, 0.5, 0.6, 0.8, 1.0]
     job = mc.Job(L, p, 9 + rank, 1)
-    kept = 0
-    done = 0
+    kept = rounds = done = 0
     t0 = time.perf_counter()
     while done < iters and time.perf_counter() - t0 < args.time_limit:
-        job.run_sweeps(S)
-        kept += job.join()
-        job.update_weights()
+        if args.mtotal > 0:
+            j, r = job.iteration(S, args.mtotal)
+            kept += j
+            rounds += r
+        else:
+            job.run_sweeps(S)
+            kept += job.join()
+            job.update_weights()
+            rounds += 1
         done += 1
     job.sync()
     el = time.perf_counter() - t0
@@ -696,10 +702,11 @@ def run_fig1(args):
             "unit": "per site", "value": max(dev["E"], dev["F"], dev["S"]), "higher_is_better": False,
             "n_gpus": 1, "data": "synthetic",
             "config": {"workload": "fig1", "L": L, "chains": p, "sweeps_per_iteration": S,
-                       "samples_per_iteration": p * S * N, "iterations": done, "iterations_asked": iters,
+                       "samples_per_round": p * S * N, "M_total": args.mtotal, "iterations": done,
+                       "iterations_asked": iters, "rounds": rounds,
                        "seed": 9 + rank, "start": "random", "betas": betas},
             "max_abs_dev": dev, "levels_visited": visited, "levels": N + 1,
-            "kept_fraction": kept / max(1, done * p * S * N), "seconds": el,
+            "kept_fraction": kept / max(1, rounds * p * S * N), "seconds": el,
             "ms_per_iteration": 1e3 * el / max(1, done), "rows": rows}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -737,7 +744,8 @@ def main(argv=None):
                          "lengthen each job)")
     ap.add_argument("--join-order", type=int, default=0,
                     help="0: chains joined in index order; 1: by ascending final energy (end of Sec. 2)")
-    ap.add_argument("--mtotal", type=int, default=100_000_000, help="fig2: samples per weight iteration (M_total)")
+    ap.add_argument("--mtotal", type=int, default=100_000_000,
+                    help="fig1, fig2: kept samples per weight iteration (M_total; fig1: 0 = one round)")
     ap.add_argument("--iters", type=int, default=0, help="fig1, fig2: weight iterations (default 1300, 20)")
     ap.add_argument("--chains", type=int, default=0, help="fig1: chains (default 4096)")
     ap.add_argument("--time-limit", type=float, default=600.0,
