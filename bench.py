@@ -156,7 +156,7 @@ def oracle_sample(seconds_budget: float, L: int, seed: int, start: int):
         el = time.perf_counter() - t0
         if el >= seconds_budget:
             break
-    return {"value": kept / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": kept / el, "unit": UNIT, "cores": cores, "per_core": kept / el / cores, "kind": "oracle",
             "sample": f"L={L}, {p} chains x {S} sweeps per iteration, {iters} weight iterations "
                       f"from the workload's seed ({el:.1f} s)"}
 
@@ -186,8 +186,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": {"workload": WORKLOAD, "L": w.L, "chains": p,
                                             "sweeps_per_iteration": S, "seed": w.seed},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "per_core": value / cores,
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
