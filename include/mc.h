@@ -346,7 +346,10 @@ int mc_sync(mc_job *job);
  *   t0        attempts each chain made before this round (multiple of 4),
  *             so that round r of a job started at t0 = 0 uses t0 = r*M.
  * Work is queued on cuda_stream (NULL = legacy default stream); returns
- * without waiting.  Scratch: the threshold table lives in one fixed
+ * without waiting.  The launch shape is the library's default for L and
+ * n_chains (see mc_set_launch_shape; at L = 96, and at L = 100, 128 with
+ * more than 8 chains a warp, the lattices are swept in place in d_spins).
+ * Scratch: the threshold table lives in one fixed
  * 320 KiB device array (L <= 128) that the library holds on every device
  * until the process exits; L > 128 is rejected with MC_EINVAL.  The first
  * call on a device looks up that array's address (cudaGetSymbolAddress)
