@@ -22,6 +22,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mc_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# A prebuilt oracle library to load instead (nothing is compiled then): the
+# mutation test uses it to run the pins against deliberately broken builds.
+_LIB_OVERRIDE = os.environ.get("MC_ORACLE_LIB", "")
 _lock = threading.Lock()
 _lib = None
 
@@ -45,8 +48,11 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = ctypes.CDLL(_LIB_PATH)
+            if _LIB_OVERRIDE:
+                L = ctypes.CDLL(_LIB_OVERRIDE)
+            else:
+                build()
+                L = ctypes.CDLL(_LIB_PATH)
             _declare(L)
             _lib = L
     return _lib
