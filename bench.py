@@ -651,11 +651,11 @@ def run_fig1(args):
     recursion from W = 0, each one round of `sweeps` sweeps on every chain
     joined by detailed balance; then E/N, C/N, F/N and S/N by Eq.
     (reweighting2) against the exact finite-lattice values (Ferdinand and
-    Fisher; Kaufman's partition function).  The paper ran 32 chains of 313
-    sweeps and repeated rounds until M_total = 1e8 samples were kept before
-    each update (step 6; `--mtotal 0`: one round per iteration).  The loop
-    stops early, at a whole iteration, once `time_limit` seconds have
-    passed."""
+    Fisher; Kaufman's partition function).  Defaults: the paper's Table 1
+    run (workload L100_p32: 32 chains of 313 sweeps, seed 9), rounds repeated
+    until M_total = 1e8 samples are kept before each update (step 6;
+    `--mtotal 0`: one round per iteration).  The loop stops early, at a
+    whole iteration, once `time_limit` seconds have passed."""
     import torch
 
     import paper_0812_2964_gb300 as mc
@@ -666,13 +666,14 @@ def run_fig1(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     mc.build()
-    L = 100
+    w = WORKLOADS["L100_p32"]
+    L = w.L
     N = L * L
-    p = args.chains or 4096
-    S = args.sweeps or 20
-    iters = args.iters or 1300
+    p = args.chains or w.chains
+    S = args.sweeps or w.sweeps
+    iters = args.iters or w.iterations
     betas = [0.1, 0.2, 0.3, 0.4, 0.42, 0.4406867935097715, 0.46, 0.5, 0.6, 0.8, 1.0]
-    job = mc.Job(L, p, 9 + rank, 1)
+    job = mc.Job(L, p, w.seed + rank, w.start)
     kept = rounds = done = 0
     t0 = time.perf_counter()
     while done < iters and time.perf_counter() - t0 < args.time_limit:
@@ -704,7 +705,7 @@ def run_fig1(args):
             "config": {"workload": "fig1", "L": L, "chains": p, "sweeps_per_iteration": S,
                        "samples_per_round": p * S * N, "M_total": args.mtotal, "iterations": done,
                        "iterations_asked": iters, "rounds": rounds,
-                       "seed": 9 + rank, "start": "random", "betas": betas},
+                       "seed": w.seed + rank, "start": "random" if w.start else "all up", "betas": betas},
             "max_abs_dev": dev, "levels_visited": visited, "levels": N + 1,
             "kept_fraction": kept / max(1, rounds * p * S * N), "seconds": el,
             "ms_per_iteration": 1e3 * el / max(1, done), "rows": rows}
@@ -747,7 +748,7 @@ def main(argv=None):
     ap.add_argument("--mtotal", type=int, default=100_000_000,
                     help="fig1, fig2: kept samples per weight iteration (M_total; fig1: 0 = one round)")
     ap.add_argument("--iters", type=int, default=0, help="fig1, fig2: weight iterations (default 1300, 20)")
-    ap.add_argument("--chains", type=int, default=0, help="fig1: chains (default 4096)")
+    ap.add_argument("--chains", type=int, default=0, help="fig1: chains (default 32, the paper's)")
     ap.add_argument("--time-limit", type=float, default=600.0,
                     help="fig1: stop after the iteration that passes this many seconds")
     ap.add_argument("--mnode", type=int, default=100, help="fig2: attempts per chain per round (M_node)")
