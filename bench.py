@@ -648,7 +648,7 @@ def run_fig2(args):
 def run_fig1(args):
     """The Fig. 1 comparison (Sec. 5) at the paper's lattice size and number
     of weight iterations: L = 100, I = 1300 iterations of the weight
-    recursion from W = 0, each one round of `sweeps` sweeps on every chain
+    recursion from W = 0, each from rounds of `sweeps` sweeps on every chain
     joined by detailed balance; then E/N, C/N, F/N and S/N by Eq.
     (reweighting2) against the exact finite-lattice values (Ferdinand and
     Fisher; Kaufman's partition function).  Defaults: the paper's Table 1
