@@ -66,6 +66,22 @@ def test_job_device_bytes_is_a_host_query(libpath):
     assert mc.mc_job_device_bytes(64, 100, 10) > a      # larger lattice, more memory
 
 
+def test_job_device_bytes_counts_the_round_record(libpath):
+    # a whole-sweep round of at most 2^33 samples is recorded, 2 bytes a
+    # sample for every chain of a tile of 32: one chain past a full tile adds
+    # a whole tile's record
+    M = 10 * 32 * 32
+    grow = mc.mc_job_device_bytes(32, 33, 10) - mc.mc_job_device_bytes(32, 32, 10)
+    assert grow >= 32 * M * 2
+    assert mc.mc_job_device_bytes(32, 34, 10) - mc.mc_job_device_bytes(32, 33, 10) < M * 2
+    # above 2^33 samples the round is replayed instead: no record (16.8 GB at
+    # 500 sweeps of 1024 chains at L = 128, 8.4e9 samples; none at 600 sweeps)
+    assert 1024 * 500 * 128 * 128 <= 2 ** 33 < 1024 * 600 * 128 * 128
+    with_rec = mc.mc_job_device_bytes(128, 1024, 500)
+    without = mc.mc_job_device_bytes(128, 1024, 600)
+    assert with_rec - without > 1024 * 500 * 128 * 128 * 2 * 0.9
+
+
 def test_load_rejects_missing_and_foreign_files(libpath, tmp_path):
     # checked before any CUDA call
     with pytest.raises(mc.McError) as e:
