@@ -92,3 +92,27 @@ def test_load_rejects_missing_and_foreign_files(libpath, tmp_path):
     with pytest.raises(mc.McError) as e:
         mc.mc_load(str(bad))
     assert e.value.code == mc.MC_EINVAL
+
+
+def test_last_error_is_per_thread(libpath):
+    # argument errors come back before any CUDA call: no GPU needed
+    import threading
+
+    msgs = {}
+
+    def fail_in_thread():
+        with pytest.raises(mc.McError):
+            mc.mc_init(3, 4, 1, 0)
+        msgs["other"] = mc.mc_last_error()
+
+    def fresh_thread():
+        msgs["fresh"] = mc.mc_last_error()
+
+    t = threading.Thread(target=fail_in_thread)
+    t.start()
+    t.join()
+    t = threading.Thread(target=fresh_thread)
+    t.start()
+    t.join()
+    assert "L=3" in msgs["other"], msgs["other"]
+    assert msgs["fresh"] == ""
