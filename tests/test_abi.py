@@ -116,3 +116,14 @@ def test_last_error_is_per_thread(libpath):
     t.join()
     assert "L=3" in msgs["other"], msgs["other"]
     assert msgs["fresh"] == ""
+
+
+def test_job_device_bytes_caps_the_checkpoints(libpath):
+    # rounds too large to record keep lattice checkpoints for the joint's
+    # replays, fewer and longer segments once they would pass 4 GiB: a job's
+    # memory stops growing with the round length
+    for L, p in [(32, 16384), (64, 4096), (128, 1024)]:
+        b1 = mc.mc_job_device_bytes(L, p, 200_000)
+        b2 = mc.mc_job_device_bytes(L, p, 1_000_000)   # (S N < 2^34 at L = 128)
+        assert b1 < 4 * 2 ** 30 + 200_000_000
+        assert abs(b2 - b1) < 0.05 * b1
