@@ -9,6 +9,10 @@ The arithmetic lives in ``mc_oracle.c`` (plain C, built with gcc
 through ctypes.  Paper sections followed: Sec. 2 (the algorithm, steps 1-6),
 Sec. 3.1 (Eq. new_weight), Sec. 4.1 (the Hamiltonian), Sec. 4.2 (weights kept
 as logarithms; Metropolis test at the joints).
+
+``MC_ORACLE_LIB`` names a prebuilt library to load instead of compiling
+``mc_oracle.c``; only the mutation test sets it, to run the pins against
+deliberately broken builds.
 """
 from __future__ import annotations
 
